@@ -1,0 +1,665 @@
+/*
+ * Plain FP64 CPU oracle of the ideal-MHD Godunov step (TEST INFRASTRUCTURE).
+ *
+ * This file is the checker, not the product.  Only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark load it.  It shares no code with
+ * the CUDA library: no header, helper or constant.
+ *
+ * What it computes (the gPLUTO method of the paper, Sec. 2.2: "reconstruction
+ * of primitive variables, Riemann problem solution at cell interfaces, and
+ * flux-conservative temporal update", with constrained transport for MHD;
+ * the paper prints no formulas, so every step follows the published method it
+ * names, written out below in the order the step performs it):
+ *
+ *   state    5 cell-centred conserved variables (rho, mx, my, mz, E) and the
+ *            three face-staggered normal field components (Bx at x-faces
+ *            i-1/2, By at y-faces j-1/2, Bz at z-faces k-1/2).
+ *   step 1   primitive recovery: v = m/rho, cell B = mean of its two faces,
+ *            p = (gamma-1)(E - |m|^2/(2 rho) - |B|^2/2), with floors.
+ *   step 2   piecewise-linear reconstruction of the 7 primitives (rho, v_n,
+ *            v_t1, v_t2, p, B_t1, B_t2) with the monotonised-central (MC)
+ *            limiter (van Leer 1977), one direction at a time.
+ *   step 3   HLLD Riemann flux (Miyoshi & Kusano 2005, JCP 208:315) per face;
+ *            HLL (Harten, Lax & van Leer 1983) as the cheap alternative.
+ *   step 4   flux divergence of the 5 hydrodynamic variables (x, y, z order).
+ *   step 5   constrained-transport edge EMFs: upwind "contact" average of
+ *            Gardiner & Stone 2005 (JCP 205:509, their eqs. 41-50), or the
+ *            arithmetic mean of the 4 face EMFs as a debug option.
+ *   step 6   face-B update dB/dt = -curl E on the staggered faces.
+ *   step 7   two-stage RK2 (Heun): U* = U + dt L(U);
+ *            U^{n+1} = (U + U* + dt L(U*))/2.
+ *   CFL      dt = C / max_cells sum_{d: n_d>1} (|v_d| + c_f,d)/Delta_d.
+ *
+ * Boundaries: periodic (wrap) or outflow (zero-gradient: ghost cells copy the
+ * nearest interior cell, tangential ghost faces are copied, the ghost normal
+ * face is extrapolated linearly so that div B = 0 in every ghost cell).
+ * Three ghost layers are filled explicitly; nothing here is fused.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
+ * arithmetic is exactly the written expression order).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NG 3                 /* ghost layers: PLM needs 2, CT transverse 1 more */
+#define ORC_PERIODIC 0
+#define ORC_OUTFLOW 1
+#define ORC_HLLD 0
+#define ORC_HLL 1
+
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  double gamma, cfl;
+  int bc[3];
+  double rho_floor, p_floor;
+  int emf_mean;     /* 0: Gardiner-Stone upwind contact average, 1: plain mean */
+  int riemann;      /* ORC_HLLD or ORC_HLL */
+} orc_cfg;
+
+typedef struct {
+  long long rho_floor_hits;
+  long long p_floor_hits;
+} orc_stats;
+
+/* ------------------------------------------------------------------------ */
+/* single-face building blocks (exported so the tests can pin them alone)    */
+/* ------------------------------------------------------------------------ */
+
+/* MC limiter: minmod(2 dm, 2 dp, (dm+dp)/2) with dm = q0-qm, dp = qp-q0. */
+double orc_mc_slope(double qm, double q0, double qp) {
+  double dm = q0 - qm, dp = qp - q0;
+  if (dm * dp <= 0.0) return 0.0;
+  double a = 2.0 * fabs(dm), b = 2.0 * fabs(dp), c = 0.5 * fabs(dm + dp);
+  double m = a < b ? a : b;
+  m = m < c ? m : c;
+  return dp > 0.0 ? m : -m;
+}
+
+/* fast magnetosonic speed along the normal for primitive w (rho, vn, vt1, vt2,
+ * p, Bt1, Bt2) and normal field bn:
+ *   c_f^2 = ( a^2 + b^2 + sqrt((a^2+b^2)^2 - 4 a^2 bn^2/rho) ) / 2,
+ *   a^2 = gamma p/rho, b^2 = |B|^2/rho. */
+double orc_fast_speed(const double *w, double bn, double gamma) {
+  double rho = w[0];
+  double a2 = gamma * w[4] / rho;
+  double b2 = (bn * bn + w[5] * w[5] + w[6] * w[6]) / rho;
+  double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * bn * bn / rho;
+  if (disc < 0.0) disc = 0.0;
+  return sqrt(0.5 * (s + sqrt(disc)));
+}
+
+/* conserved 7-vector (rho, rho vn, rho vt1, rho vt2, E, Bt1, Bt2) */
+static void w_to_u7(const double *w, double bn, double gamma, double *u) {
+  double rho = w[0];
+  u[0] = rho;
+  u[1] = rho * w[1];
+  u[2] = rho * w[2];
+  u[3] = rho * w[3];
+  u[4] = w[4] / (gamma - 1.0) +
+         0.5 * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
+         0.5 * (bn * bn + w[5] * w[5] + w[6] * w[6]);
+  u[5] = w[5];
+  u[6] = w[6];
+}
+
+/* physical flux of ideal MHD along the normal (Bx = bn constant) */
+void orc_phys_flux(const double *w, double bn, double gamma, double *f) {
+  double rho = w[0], u = w[1], v = w[2], ww = w[3], p = w[4];
+  double by = w[5], bz = w[6];
+  double b2 = bn * bn + by * by + bz * bz;
+  double pt = p + 0.5 * b2;
+  double e = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + ww * ww) + 0.5 * b2;
+  double vb = u * bn + v * by + ww * bz;
+  f[0] = rho * u;
+  f[1] = rho * u * u + pt - bn * bn;
+  f[2] = rho * u * v - bn * by;
+  f[3] = rho * u * ww - bn * bz;
+  f[4] = (e + pt) * u - bn * vb;
+  f[5] = u * by - v * bn;
+  f[6] = u * bz - ww * bn;
+}
+
+/* HLL flux: F = (SR FL - SL FR + SL SR (UR - UL)) / (SR - SL) inside the fan. */
+void orc_hll(const double *wl, const double *wr, double bn, double gamma, double *f) {
+  double cl = orc_fast_speed(wl, bn, gamma), cr = orc_fast_speed(wr, bn, gamma);
+  double cmax = cl > cr ? cl : cr;
+  double sl = (wl[1] < wr[1] ? wl[1] : wr[1]) - cmax;
+  double sr = (wl[1] > wr[1] ? wl[1] : wr[1]) + cmax;
+  double fl[7], fr[7], ul[7], ur[7];
+  orc_phys_flux(wl, bn, gamma, fl);
+  orc_phys_flux(wr, bn, gamma, fr);
+  if (sl >= 0.0) { memcpy(f, fl, 7 * sizeof(double)); return; }
+  if (sr <= 0.0) { memcpy(f, fr, 7 * sizeof(double)); return; }
+  w_to_u7(wl, bn, gamma, ul);
+  w_to_u7(wr, bn, gamma, ur);
+  for (int q = 0; q < 7; ++q)
+    f[q] = (sr * fl[q] - sl * fr[q] + sl * sr * (ur[q] - ul[q])) / (sr - sl);
+}
+
+/* HLLD flux of Miyoshi & Kusano (2005).  Star states from their eqs. (38),
+ * (23), (43)-(48); outer Alfven speeds eq. (51); double-star states eqs.
+ * (59)-(63); fluxes eqs. (64)-(66).  Readings where the paper is silent:
+ *   - degenerate star state (den ~ 0): v*, B* keep the outer values when
+ *     |den| <= 1e-12 max(|rho (S-u)(S-SM)|, bn^2);
+ *   - sign(0) = 0;
+ *   - ties at exactly zero take the first listed region, scanning
+ *     L, L*, L**, R**, R*, R. */
+void orc_hlld(const double *wl, const double *wr, double bn, double gamma, double *f) {
+  const double eps = 1e-12;
+  double cl = orc_fast_speed(wl, bn, gamma), cr = orc_fast_speed(wr, bn, gamma);
+  double cmax = cl > cr ? cl : cr;
+  double sl = (wl[1] < wr[1] ? wl[1] : wr[1]) - cmax;
+  double sr = (wl[1] > wr[1] ? wl[1] : wr[1]) + cmax;
+  double fl[7], fr[7], ul[7], ur[7];
+  orc_phys_flux(wl, bn, gamma, fl);
+  orc_phys_flux(wr, bn, gamma, fr);
+  if (sl > 0.0) { memcpy(f, fl, 7 * sizeof(double)); return; }
+  if (sr < 0.0) { memcpy(f, fr, 7 * sizeof(double)); return; }
+  w_to_u7(wl, bn, gamma, ul);
+  w_to_u7(wr, bn, gamma, ur);
+
+  double rl = wl[0], rr = wr[0], uL = wl[1], uR = wr[1];
+  double ptl = wl[4] + 0.5 * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6]);
+  double ptr = wr[4] + 0.5 * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6]);
+  double sdl = sl - uL, sdr = sr - uR;
+  double sm = (sdr * rr * uR - sdl * rl * uL - ptr + ptl) / (sdr * rr - sdl * rl);
+  double pts = ptl + rl * sdl * (sm - uL);
+
+  /* single-star states on each side */
+  const double *w[2] = {wl, wr};
+  const double *uo[2] = {ul, ur};
+  double s[2] = {sl, sr}, sd[2] = {sdl, sdr};
+  double us[2][7], vbs[2], sqr[2], vsa[2], wsa[2];
+  for (int a = 0; a < 2; ++a) {
+    double rho = w[a][0], u = w[a][1], v = w[a][2], ww = w[a][3];
+    double by = w[a][5], bz = w[a][6];
+    double rhos = rho * sd[a] / (s[a] - sm);
+    double num = rho * sd[a] * (s[a] - sm);
+    double den = num - bn * bn;
+    double scale = fabs(num) > bn * bn ? fabs(num) : bn * bn;
+    double vs, ws, bys, bzs;
+    if (fabs(den) <= eps * scale) {
+      vs = v; ws = ww; bys = by; bzs = bz;
+    } else {
+      vs = v - bn * by * (sm - u) / den;
+      ws = ww - bn * bz * (sm - u) / den;
+      bys = by * (rho * sd[a] * sd[a] - bn * bn) / den;
+      bzs = bz * (rho * sd[a] * sd[a] - bn * bn) / den;
+    }
+    double vb = u * bn + v * by + ww * bz;
+    vbs[a] = sm * bn + vs * bys + ws * bzs;
+    vsa[a] = vs;
+    wsa[a] = ws;
+    double pt = a == 0 ? ptl : ptr;
+    double es = (sd[a] * uo[a][4] - pt * u + pts * sm + bn * (vb - vbs[a])) / (s[a] - sm);
+    us[a][0] = rhos;
+    us[a][1] = rhos * sm;
+    us[a][2] = rhos * vs;
+    us[a][3] = rhos * ws;
+    us[a][4] = es;
+    us[a][5] = bys;
+    us[a][6] = bzs;
+    sqr[a] = sqrt(rhos);
+  }
+  double ssl = sm - fabs(bn) / sqr[0];
+  double ssr = sm + fabs(bn) / sqr[1];
+
+  if (ssl >= 0.0) {            /* left single-star region */
+    for (int q = 0; q < 7; ++q) f[q] = fl[q] + sl * (us[0][q] - ul[q]);
+    return;
+  }
+  if (sm < 0.0 && ssr < 0.0) { /* right single-star region */
+    for (int q = 0; q < 7; ++q) f[q] = fr[q] + sr * (us[1][q] - ur[q]);
+    return;
+  }
+  /* double-star states */
+  double sgn = bn > 0.0 ? 1.0 : (bn < 0.0 ? -1.0 : 0.0);
+  double sq = sqr[0] + sqr[1];
+  double vl_ = vsa[0], wl_ = wsa[0], vr_ = vsa[1], wr_ = wsa[1];
+  double vss = (sqr[0] * vl_ + sqr[1] * vr_ + (us[1][5] - us[0][5]) * sgn) / sq;
+  double wss = (sqr[0] * wl_ + sqr[1] * wr_ + (us[1][6] - us[0][6]) * sgn) / sq;
+  double byss = (sqr[0] * us[1][5] + sqr[1] * us[0][5] + sqr[0] * sqr[1] * (vr_ - vl_) * sgn) / sq;
+  double bzss = (sqr[0] * us[1][6] + sqr[1] * us[0][6] + sqr[0] * sqr[1] * (wr_ - wl_) * sgn) / sq;
+  double vbss = sm * bn + vss * byss + wss * bzss;
+  int a = sm >= 0.0 ? 0 : 1;
+  double ess = a == 0 ? us[0][4] - sqr[0] * (vbs[0] - vbss) * sgn
+                      : us[1][4] + sqr[1] * (vbs[1] - vbss) * sgn;
+  double uss[7];
+  uss[0] = us[a][0];
+  uss[1] = us[a][0] * sm;
+  uss[2] = us[a][0] * vss;
+  uss[3] = us[a][0] * wss;
+  uss[4] = ess;
+  uss[5] = byss;
+  uss[6] = bzss;
+  const double *fo = a == 0 ? fl : fr;
+  const double *uu = a == 0 ? ul : ur;
+  double so = a == 0 ? sl : sr, sso = a == 0 ? ssl : ssr;
+  for (int q = 0; q < 7; ++q)
+    f[q] = fo[q] + so * (us[a][q] - uu[q]) + sso * (uss[q] - us[a][q]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* grid with explicit ghost layers                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const orc_cfg *c;
+  int n[3];      /* interior cells */
+  int N[3];      /* extended cells: n + 2 NG */
+  int nf[3];     /* stored faces along each normal: n (periodic) or n+1 */
+  size_t ncell;  /* extended cell count */
+  size_t nedge;  /* (N+1)^3 style count for face/edge arrays */
+} grid;
+
+static size_t cidx(const grid *g, int I, int J, int K) {
+  return (size_t)I + (size_t)g->N[0] * ((size_t)J + (size_t)g->N[1] * (size_t)K);
+}
+/* face/edge arrays use (N+1) points per axis */
+static size_t fidx(const grid *g, int I, int J, int K) {
+  return (size_t)I + (size_t)(g->N[0] + 1) * ((size_t)J + (size_t)(g->N[1] + 1) * (size_t)K);
+}
+
+static int wrap_or_clamp(int i, int n, int bc) {
+  if (bc == ORC_PERIODIC) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+/* stored face array of normal d at interior coordinates (i,j,k); the normal
+ * index i_d may lie outside [0, nf): periodic wraps, outflow extrapolates. */
+static double face_value(const grid *g, double *const face[3], int d, int ijk[3]) {
+  int t[3];
+  for (int e = 0; e < 3; ++e)
+    if (e != d) t[e] = wrap_or_clamp(ijk[e], g->n[e], g->c->bc[e]);
+  const double *b = face[d];
+  int len[3] = {g->n[0], g->n[1], g->n[2]};
+  len[d] = g->nf[d];
+#define FACE_AT(ii) (t[d] = (ii), b[(size_t)t[0] + (size_t)len[0] * ((size_t)t[1] + (size_t)len[1] * (size_t)t[2])])
+  int i = ijk[d];
+  if (g->c->bc[d] == ORC_PERIODIC) {
+    int r = wrap_or_clamp(i, g->n[d], ORC_PERIODIC);
+    return FACE_AT(r);
+  }
+  int n = g->n[d];
+  if (i >= 0 && i <= n) return FACE_AT(i);
+  if (i < 0) {
+    double b0 = FACE_AT(0), b1 = FACE_AT(1);
+    return b0 + (double)i * (b1 - b0);
+  }
+  double bn = FACE_AT(n), bm = FACE_AT(n - 1);
+  return bn + (double)(i - n) * (bn - bm);
+#undef FACE_AT
+}
+
+/* ------------------------------------------------------------------------ */
+/* one evaluation of the spatial operator L(U)                               */
+/* ------------------------------------------------------------------------ */
+
+/* W: 8 primitive arrays on extended cells (rho, vx, vy, vz, p, Bcx, Bcy, Bcz)
+ * Bf: 3 face arrays on the extended (N+1)^3 lattice (face index I = left face
+ * of extended cell I). */
+static void build_primitives(const grid *g, double *const cell[5], double *const face[3],
+                             double *W[8], double *Bf[3], orc_stats *st) {
+  const orc_cfg *c = g->c;
+  for (int K = 0; K <= g->N[2]; ++K)
+    for (int J = 0; J <= g->N[1]; ++J)
+      for (int I = 0; I <= g->N[0]; ++I) {
+        int ijk[3] = {I - NG, J - NG, K - NG};
+        for (int d = 0; d < 3; ++d) {
+          int a[3] = {ijk[0], ijk[1], ijk[2]};
+          Bf[d][fidx(g, I, J, K)] = face_value(g, face, d, a);
+        }
+      }
+  for (int K = 0; K < g->N[2]; ++K)
+    for (int J = 0; J < g->N[1]; ++J)
+      for (int I = 0; I < g->N[0]; ++I) {
+        int i = wrap_or_clamp(I - NG, g->n[0], c->bc[0]);
+        int j = wrap_or_clamp(J - NG, g->n[1], c->bc[1]);
+        int k = wrap_or_clamp(K - NG, g->n[2], c->bc[2]);
+        size_t s = (size_t)i + (size_t)g->n[0] * ((size_t)j + (size_t)g->n[1] * (size_t)k);
+        double rho = cell[0][s], mx = cell[1][s], my = cell[2][s], mz = cell[3][s], e = cell[4][s];
+        double bx = 0.5 * (Bf[0][fidx(g, I, J, K)] + Bf[0][fidx(g, I + 1, J, K)]);
+        double by = 0.5 * (Bf[1][fidx(g, I, J, K)] + Bf[1][fidx(g, I, J + 1, K)]);
+        double bz = 0.5 * (Bf[2][fidx(g, I, J, K)] + Bf[2][fidx(g, I, J, K + 1)]);
+        int interior = I >= NG && I < NG + g->n[0] && J >= NG && J < NG + g->n[1] &&
+                       K >= NG && K < NG + g->n[2];
+        if (rho < c->rho_floor) {
+          rho = c->rho_floor;
+          if (interior && st) st->rho_floor_hits++;
+        }
+        double p = (c->gamma - 1.0) *
+                   (e - 0.5 * (mx * mx + my * my + mz * mz) / rho - 0.5 * (bx * bx + by * by + bz * bz));
+        if (p < c->p_floor) {
+          p = c->p_floor;
+          if (interior && st) st->p_floor_hits++;
+        }
+        size_t q = cidx(g, I, J, K);
+        W[0][q] = rho;
+        W[1][q] = mx / rho;
+        W[2][q] = my / rho;
+        W[3][q] = mz / rho;
+        W[4][q] = p;
+        W[5][q] = bx;
+        W[6][q] = by;
+        W[7][q] = bz;
+      }
+}
+
+/* rotated order of the primitives for a sweep along d:
+ * (rho, v_n, v_t1, v_t2, p, B_t1, B_t2) with (n, t1, t2) cyclic. */
+static void rotated(const grid *g, double *W[8], int d, size_t q, double *w) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  (void)g;
+  w[0] = W[0][q];
+  w[1] = W[1 + d][q];
+  w[2] = W[1 + t1][q];
+  w[3] = W[1 + t2][q];
+  w[4] = W[4][q];
+  w[5] = W[5 + t1][q];
+  w[6] = W[5 + t2][q];
+}
+
+/* face fluxes along d for every face whose 4-cell stencil lies in the
+ * extended grid.  F[q] (q = 0..6, rotated order) is stored at the (N+1)^3
+ * lattice index of the face's right cell (face I = left face of cell I). */
+static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7]) {
+  const orc_cfg *c = g->c;
+  int lo[3] = {0, 0, 0}, hi[3] = {g->N[0], g->N[1], g->N[2]};
+  lo[d] = 2;
+  hi[d] = g->N[d] - 1;   /* faces I in [2, N-1): cells I-2 .. I+1 exist */
+  int off[3] = {0, 0, 0};
+  off[d] = 1;
+  size_t st = (size_t)off[0] + (size_t)g->N[0] * ((size_t)off[1] + (size_t)g->N[1] * (size_t)off[2]);
+  for (int K = lo[2]; K < hi[2]; ++K)
+    for (int J = lo[1]; J < hi[1]; ++J)
+      for (int I = lo[0]; I < hi[0]; ++I) {
+        size_t q0 = cidx(g, I, J, K);          /* right cell of the face */
+        double wm2[7], wm1[7], w0[7], wp1[7];
+        rotated(g, W, d, q0 - 2 * st, wm2);
+        rotated(g, W, d, q0 - st, wm1);
+        rotated(g, W, d, q0, w0);
+        rotated(g, W, d, q0 + st, wp1);
+        /* left cell (I-1): slopes from I-2, I-1, I;  right cell (I): I-1, I, I+1 */
+        double sL[7], sR[7], wl[7], wr[7];
+        for (int v = 0; v < 7; ++v) {
+          sL[v] = orc_mc_slope(wm2[v], wm1[v], w0[v]);
+          sR[v] = orc_mc_slope(wm1[v], w0[v], wp1[v]);
+        }
+        /* positivity: a cell whose reconstructed face values of rho or p
+         * would be <= 0 uses zero slopes in this direction */
+        if (wm1[0] - 0.5 * sL[0] <= 0.0 || wm1[0] + 0.5 * sL[0] <= 0.0 ||
+            wm1[4] - 0.5 * sL[4] <= 0.0 || wm1[4] + 0.5 * sL[4] <= 0.0)
+          for (int v = 0; v < 7; ++v) sL[v] = 0.0;
+        if (w0[0] - 0.5 * sR[0] <= 0.0 || w0[0] + 0.5 * sR[0] <= 0.0 ||
+            w0[4] - 0.5 * sR[4] <= 0.0 || w0[4] + 0.5 * sR[4] <= 0.0)
+          for (int v = 0; v < 7; ++v) sR[v] = 0.0;
+        for (int v = 0; v < 7; ++v) {
+          wl[v] = wm1[v] + 0.5 * sL[v];
+          wr[v] = w0[v] - 0.5 * sR[v];
+        }
+        double bn = Bf[d][fidx(g, I, J, K)];
+        double f[7];
+        if (c->riemann == ORC_HLL) orc_hll(wl, wr, bn, c->gamma, f);
+        else orc_hlld(wl, wr, bn, c->gamma, f);
+        size_t fq = fidx(g, I, J, K);
+        for (int v = 0; v < 7; ++v) F[v][fq] = f[v];
+      }
+}
+
+/* Gardiner & Stone (2005) upwind selection: lo if the mass flux is > 0,
+ * hi if it is < 0, their mean otherwise. */
+static double upwind(double mflux, double lo, double hi) {
+  if (mflux > 0.0) return lo;
+  if (mflux < 0.0) return hi;
+  return 0.5 * (lo + hi);
+}
+
+/* full spatial operator: dU (5 cell arrays) and dB (3 face arrays) in the
+ * caller's storage layout. */
+static void spatial_operator(const orc_cfg *c, double *const cell[5], double *const face[3],
+                             double *dU[5], double *dB[3], orc_stats *st) {
+  grid g;
+  g.c = c;
+  g.n[0] = c->nx; g.n[1] = c->ny; g.n[2] = c->nz;
+  for (int d = 0; d < 3; ++d) {
+    g.N[d] = g.n[d] + 2 * NG;
+    g.nf[d] = g.n[d] + (c->bc[d] == ORC_OUTFLOW ? 1 : 0);
+  }
+  g.ncell = (size_t)g.N[0] * g.N[1] * g.N[2];
+  g.nedge = (size_t)(g.N[0] + 1) * (g.N[1] + 1) * (g.N[2] + 1);
+
+  double *W[8], *Bf[3], *F[3][7], *Ec[3], *Ed[3];
+  for (int v = 0; v < 8; ++v) W[v] = calloc(g.ncell, sizeof(double));
+  for (int d = 0; d < 3; ++d) {
+    Bf[d] = calloc(g.nedge, sizeof(double));
+    Ec[d] = calloc(g.ncell, sizeof(double));
+    Ed[d] = calloc(g.nedge, sizeof(double));
+    for (int v = 0; v < 7; ++v) F[d][v] = calloc(g.nedge, sizeof(double));
+  }
+  build_primitives(&g, cell, face, W, Bf, st);
+  for (int d = 0; d < 3; ++d) sweep(&g, W, Bf, d, F[d]);
+
+  /* cell-centred reference EMF E_c = -v x B_c */
+  for (size_t q = 0; q < g.ncell; ++q) {
+    double vx = W[1][q], vy = W[2][q], vz = W[3][q];
+    double bx = W[5][q], by = W[6][q], bz = W[7][q];
+    Ec[0][q] = vz * by - vy * bz;
+    Ec[1][q] = vx * bz - vz * bx;
+    Ec[2][q] = vy * bx - vx * by;
+  }
+
+  /* edge EMFs.  Edge along c at the corner (a-1/2, b-1/2) of the plane of
+   * directions (a, b) = (c+1, c+2) cyclic.  Face EMFs from the fluxes of the
+   * transverse field: an a-face carries E_c = -F_a(B_b) (B_b is its t1), a
+   * b-face carries E_c = +F_b(B_a) (B_a is its t2). */
+  for (int cdir = 0; cdir < 3; ++cdir) {
+    int a = (cdir + 1) % 3, b = (cdir + 2) % 3;
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) { lo[e] = NG; hi[e] = NG + g.n[e]; }
+    hi[a] += 1;    /* edges at a-1/2 for a in [0, n_a] */
+    hi[b] += 1;
+    for (int K = lo[2]; K < hi[2]; ++K)
+      for (int J = lo[1]; J < hi[1]; ++J)
+        for (int I = lo[0]; I < hi[0]; ++I) {
+          int P[3] = {I, J, K};
+          int Pam[3] = {I, J, K}, Pbm[3] = {I, J, K}, Pabm[3] = {I, J, K};
+          Pam[a] -= 1; Pbm[b] -= 1; Pabm[a] -= 1; Pabm[b] -= 1;
+          /* a-faces at (a-1/2, b-1) and (a-1/2, b); t1 of an a-sweep is b */
+          double fa_m = -F[a][5][fidx(&g, Pbm[0], Pbm[1], Pbm[2])];
+          double fa_p = -F[a][5][fidx(&g, P[0], P[1], P[2])];
+          double ma_m = F[a][0][fidx(&g, Pbm[0], Pbm[1], Pbm[2])];
+          double ma_p = F[a][0][fidx(&g, P[0], P[1], P[2])];
+          /* b-faces at (a-1, b-1/2) and (a, b-1/2); t2 of a b-sweep is a */
+          double fb_m = F[b][6][fidx(&g, Pam[0], Pam[1], Pam[2])];
+          double fb_p = F[b][6][fidx(&g, P[0], P[1], P[2])];
+          double mb_m = F[b][0][fidx(&g, Pam[0], Pam[1], Pam[2])];
+          double mb_p = F[b][0][fidx(&g, P[0], P[1], P[2])];
+          /* cell-centred values: (a-1,b-1), (a,b-1), (a-1,b), (a,b) */
+          double e_mm = Ec[cdir][cidx(&g, Pabm[0], Pabm[1], Pabm[2])];
+          double e_pm = Ec[cdir][cidx(&g, Pbm[0], Pbm[1], Pbm[2])];
+          double e_mp = Ec[cdir][cidx(&g, Pam[0], Pam[1], Pam[2])];
+          double e_pp = Ec[cdir][cidx(&g, P[0], P[1], P[2])];
+          double avg = 0.25 * (fa_m + fa_p + fb_m + fb_p);
+          double edge;
+          if (c->emf_mean) {
+            edge = avg;
+          } else {
+            /* derivatives along b on the a-face line, upwinded by the a-face
+             * mass flux; along a on the b-face line, by the b-face mass flux */
+            double db_plus = upwind(ma_p, e_mp - fb_m, e_pp - fb_p);   /* at b-1/4 */
+            double db_minus = upwind(ma_m, fb_m - e_mm, fb_p - e_pm);  /* at b-3/4 */
+            double da_plus = upwind(mb_p, e_pm - fa_m, e_pp - fa_p);   /* at a-1/4 */
+            double da_minus = upwind(mb_m, fa_m - e_mm, fa_p - e_mp);  /* at a-3/4 */
+            edge = avg + 0.25 * (db_minus - db_plus) + 0.25 * (da_minus - da_plus);
+          }
+          Ed[cdir][fidx(&g, I, J, K)] = edge;
+        }
+  }
+
+  /* flux divergence, summed x then y then z */
+  double inv[3] = {c->dx, c->dy, c->dz};
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        size_t s = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * (size_t)k);
+        int I = i + NG, J = j + NG, K = k + NG;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+          int Q[3] = {I, J, K};
+          size_t fm = fidx(&g, Q[0], Q[1], Q[2]);
+          Q[d] += 1;
+          size_t fp = fidx(&g, Q[0], Q[1], Q[2]);
+          int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          /* rotated flux slots back to (rho, mx, my, mz, E) */
+          int slot[5];
+          slot[0] = 0;
+          slot[1 + d] = 1;
+          slot[1 + t1] = 2;
+          slot[1 + t2] = 3;
+          slot[4] = 4;
+          for (int v = 0; v < 5; ++v)
+            acc[v] = acc[v] - (F[d][slot[v]][fp] - F[d][slot[v]][fm]) / inv[d];
+        }
+        for (int v = 0; v < 5; ++v) dU[v][s] = acc[v];
+      }
+
+  /* face-B update dB/dt = -curl E */
+  for (int d = 0; d < 3; ++d) {
+    int a = (d + 1) % 3, b = (d + 2) % 3;
+    int len[3] = {g.n[0], g.n[1], g.n[2]};
+    len[d] = g.nf[d];
+    for (int k = 0; k < len[2]; ++k)
+      for (int j = 0; j < len[1]; ++j)
+        for (int i = 0; i < len[0]; ++i) {
+          int P[3] = {i + NG, j + NG, k + NG};
+          int Pa[3] = {P[0], P[1], P[2]}, Pb[3] = {P[0], P[1], P[2]};
+          Pa[a] += 1;
+          Pb[b] += 1;
+          /* (curl E)_d = dE_b/da - dE_a/db  (d, a, b cyclic) */
+          double deb = (Ed[b][fidx(&g, Pa[0], Pa[1], Pa[2])] - Ed[b][fidx(&g, P[0], P[1], P[2])]) / inv[a];
+          double dea = (Ed[a][fidx(&g, Pb[0], Pb[1], Pb[2])] - Ed[a][fidx(&g, P[0], P[1], P[2])]) / inv[b];
+          size_t s = (size_t)i + (size_t)len[0] * ((size_t)j + (size_t)len[1] * (size_t)k);
+          dB[d][s] = -(deb - dea);
+        }
+  }
+
+  for (int v = 0; v < 8; ++v) free(W[v]);
+  for (int d = 0; d < 3; ++d) {
+    free(Bf[d]);
+    free(Ec[d]);
+    free(Ed[d]);
+    for (int v = 0; v < 7; ++v) free(F[d][v]);
+  }
+}
+
+static size_t face_count(const orc_cfg *c, int d) {
+  size_t n[3] = {(size_t)c->nx, (size_t)c->ny, (size_t)c->nz};
+  if (c->bc[d] == ORC_OUTFLOW) n[d] += 1;
+  return n[0] * n[1] * n[2];
+}
+
+/* L(U): exported for the tests. */
+void orc_rhs(const orc_cfg *c, double *const cell[5], double *const face[3],
+             double *dU[5], double *dB[3], orc_stats *st) {
+  spatial_operator(c, cell, face, dU, dB, st);
+}
+
+/* One RK2 (Heun) step in place:
+ *   U*      = U^n + dt L(U^n)
+ *   U^{n+1} = (U^n + U* + dt L(U*)) / 2
+ * for the 5 cell arrays and the 3 face arrays alike. */
+void orc_step(const orc_cfg *c, double *cell[5], double *face[3], double dt, orc_stats *st) {
+  size_t nc = (size_t)c->nx * c->ny * c->nz;
+  size_t nfc[3] = {face_count(c, 0), face_count(c, 1), face_count(c, 2)};
+  double *us[5], *bs[3], *du[5], *db[3];
+  for (int v = 0; v < 5; ++v) { us[v] = malloc(nc * sizeof(double)); du[v] = malloc(nc * sizeof(double)); }
+  for (int d = 0; d < 3; ++d) { bs[d] = malloc(nfc[d] * sizeof(double)); db[d] = malloc(nfc[d] * sizeof(double)); }
+
+  spatial_operator(c, cell, face, du, db, st);
+  for (int v = 0; v < 5; ++v)
+    for (size_t s = 0; s < nc; ++s) us[v][s] = cell[v][s] + dt * du[v][s];
+  for (int d = 0; d < 3; ++d)
+    for (size_t s = 0; s < nfc[d]; ++s) bs[d][s] = face[d][s] + dt * db[d][s];
+
+  spatial_operator(c, us, bs, du, db, st);
+  for (int v = 0; v < 5; ++v)
+    for (size_t s = 0; s < nc; ++s) cell[v][s] = 0.5 * (cell[v][s] + us[v][s] + dt * du[v][s]);
+  for (int d = 0; d < 3; ++d)
+    for (size_t s = 0; s < nfc[d]; ++s) face[d][s] = 0.5 * (face[d][s] + bs[d][s] + dt * db[d][s]);
+
+  for (int v = 0; v < 5; ++v) { free(us[v]); free(du[v]); }
+  for (int d = 0; d < 3; ++d) { free(bs[d]); free(db[d]); }
+}
+
+/* CFL time step dt = C / max over cells of sum_{d: n_d > 1} (|v_d| + c_f,d)/Delta_d,
+ * the fast speed along d taken with the cell-centred B_d as the normal field. */
+double orc_cfl_dt(const orc_cfg *c, double *const cell[5], double *const face[3]) {
+  int n[3] = {c->nx, c->ny, c->nz};
+  double del[3] = {c->dx, c->dy, c->dz};
+  double smax = 0.0;
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        size_t s = (size_t)i + (size_t)n[0] * ((size_t)j + (size_t)n[1] * (size_t)k);
+        double bc[3];
+        for (int d = 0; d < 3; ++d) {
+          int len[3] = {n[0], n[1], n[2]};
+          if (c->bc[d] == ORC_OUTFLOW) len[d] += 1;
+          int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+          hi[d] += 1;
+          if (c->bc[d] == ORC_PERIODIC && hi[d] == n[d]) hi[d] = 0;
+          double bl = face[d][(size_t)lo[0] + (size_t)len[0] * ((size_t)lo[1] + (size_t)len[1] * (size_t)lo[2])];
+          double br = face[d][(size_t)hi[0] + (size_t)len[0] * ((size_t)hi[1] + (size_t)len[1] * (size_t)hi[2])];
+          bc[d] = 0.5 * (bl + br);
+        }
+        double rho = cell[0][s];
+        if (rho < c->rho_floor) rho = c->rho_floor;
+        double v[3] = {cell[1][s] / rho, cell[2][s] / rho, cell[3][s] / rho};
+        double p = (c->gamma - 1.0) *
+                   (cell[4][s] - 0.5 * (cell[1][s] * cell[1][s] + cell[2][s] * cell[2][s] +
+                                        cell[3][s] * cell[3][s]) / rho -
+                    0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+        if (p < c->p_floor) p = c->p_floor;
+        double sum = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          if (n[d] <= 1) continue;
+          int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          double w[7] = {rho, v[d], v[t1], v[t2], p, bc[t1], bc[t2]};
+          double cf = orc_fast_speed(w, bc[d], c->gamma);
+          sum = sum + (fabs(v[d]) + cf) / del[d];
+        }
+        if (sum > smax) smax = sum;
+      }
+  return c->cfl / smax;
+}
+
+/* max over cells of |div B| (the face-difference divergence). */
+double orc_divb_max(const orc_cfg *c, double *const face[3]) {
+  int n[3] = {c->nx, c->ny, c->nz};
+  double del[3] = {c->dx, c->dy, c->dz};
+  double m = 0.0;
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        double div = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          int len[3] = {n[0], n[1], n[2]};
+          if (c->bc[d] == ORC_OUTFLOW) len[d] += 1;
+          int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+          hi[d] += 1;
+          if (c->bc[d] == ORC_PERIODIC && hi[d] == n[d]) hi[d] = 0;
+          double bl = face[d][(size_t)lo[0] + (size_t)len[0] * ((size_t)lo[1] + (size_t)len[1] * (size_t)lo[2])];
+          double br = face[d][(size_t)hi[0] + (size_t)len[0] * ((size_t)hi[1] + (size_t)len[1] * (size_t)hi[2])];
+          div = div + (br - bl) / del[d];
+        }
+        if (fabs(div) > m) m = fabs(div);
+      }
+  return m;
+}
