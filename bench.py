@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MHD hot path: Mcell-updates/s of the RK2 Godunov
+step (PLM-MC + HLLD + upwind CT + RK2 + device CFL) on the 3D decaying
+turbulence box, 256^3 periodic, mixed FP32/FP64 precision.
+
+One "step" is one full RK2 step (both fused stage kernels, with the CFL
+max-reduction fused into stage 1 and the self-computed dt used by stage 2)
+over the whole box.  Inputs are generated from the seeded turbulence recipe
+(synthetic; the paper's runs use no dataset).  The state (2.7 GB with the
+stage buffer) is far larger than the 129 MB L2, so no flush is needed between
+steps.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle instead (on a bounded sample of the same workload).
+Multi-GPU (torchrun, N > 1): every rank advances its own replica box (the
+single-box path is not sharded); value = cells x steps x N / max-over-ranks
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-updates/s on 1 GB300 at 256^3 MHD; % HBM roofline; vs plain FP64 at L1 error"
+UNIT = "Mcell-updates/s"
+# algorithmic HBM bytes per cell per stage kernel launch (read + write, fully fused)
+STAGE_BYTES = {"fp64": (128, 192), "mixed": (96, 160), "fp32": (64, 96)}
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--tile", default="0,0,0")
+    p.add_argument("--compare-steps", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names[1:], parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        except FileNotFoundError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles(kernel_tag):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.txt for this
+    kernel, if the kernel sources are unchanged since the capture."""
+    from paper_2606_12753_gb300 import _build
+    import hashlib
+    h = hashlib.sha1()
+    for p in _build._deps():
+        if p.endswith((".cu", ".cuh")):
+            h.update(open(p, "rb").read())
+    digest = h.hexdigest()[:12]
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if f.get("kernel") == kernel_tag and f.get("src") == digest:
+                return float(f["dram_bytes_per_launch"]), digest
+    except FileNotFoundError:
+        pass
+    return None, digest
+
+
+def cpu_oracle_rate(seconds: float, n: int = 64):
+    """Time the FP64 oracle (as it stands, one host thread) on an n^3 sample
+    of the turbulence workload until ``seconds`` of CPU work have run."""
+    import oracle as O
+    from paper_2606_12753_gb300 import inputs as I
+    box = I.turbulence_3d(n)
+    cfg = O.Config(box.nx, box.ny, box.nz, box.dx, box.dy, box.dz, box.gamma, 0.4, box.bc)
+    cell, face = box.cell, box.face
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 1000:
+            break
+    return {"value": box.ncell * steps / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"turbulence_3d recipe at {n}^3, {steps} RK2 steps with CFL dt, single host thread, {el:.1f} s"}
+
+
+def workload_config(args):
+    return {"workload": f"turbulence_3d_{args.n}: 3D decaying MHD turbulence {args.n}^3 periodic, "
+                        f"rho=1 p=0.6 rms Mach 1 beta=1, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
+            "precision": args.precision, "n": args.n}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2606_12753_gb300 import inputs as I
+    O.build()
+    n = 48
+    box = I.turbulence_3d(n)
+    cfg = O.Config(box.nx, box.ny, box.nz, box.dx, box.dy, box.dz, box.gamma, 0.4, box.bc)
+    cell, face = box.cell, box.face
+    for _ in range(args.warmup):
+        cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
+    el = time.perf_counter() - t0
+    value = box.ncell * args.steps / el / 1e6
+    sample = f"turbulence_3d recipe at {n}^3 (each step one RK2 step of the FP64 oracle, one host thread)"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": dict(workload_config(args), sample=f"{n}^3 per step, FP64 oracle"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2606_12753_gb300 import inputs as I
+    from paper_2606_12753_gb300 import mhd
+
+    tile = tuple(int(x) for x in args.tile.split(","))
+    box = I.turbulence_3d(args.n, seed=2606)
+    stream = torch.cuda.Stream()
+    solver = mhd.Solver(box, precision=args.precision, tile=tile, stream=stream.cuda_stream)
+    solver.set_state(box.cell, box.face)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    solver.step_async(-1.0, args.warmup)
+    solver.stats()
+    solver.set_profiling(True)
+    solver.profile()
+    barrier()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step_async(-1.0, args.steps)
+        e1.record(stream)
+        stream.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, launches = solver.profile()
+    solver.set_profiling(False)
+    st = solver.stats()
+    if st["status"] != 0:
+        raise RuntimeError(f"device status {st['status']} after the timed steps")
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * box.ncell * args.steps / (ms_total / 1e3) / 1e6
+
+    peak, peak_kind = peaks()
+    k = 0 if stage_ms[0] >= stage_ms[1] else 1
+    per_launch_ms = stage_ms[k] / max(launches[k], 1)
+    alg_bytes = STAGE_BYTES[args.precision][k] * box.ncell
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    tag = f"stage_kernel<{args.precision},{k + 1}>@turbulence_3d_{args.n}"
+    traffic, src = traffic_from_profiles(tag)
+    elem = 4 if args.precision == "fp32" else 8
+    kelem = 8 if args.precision == "fp64" else 4
+    resident = box.ncell * 8 * (2 * elem + kelem)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+        "data": "synthetic",
+        "config": {**workload_config(args),
+                   "tile": [solver.cfg.tile_x, solver.cfg.tile_y, solver.cfg.tile_z],
+                   "l2": f"inputs larger than L2 (state + stage buffers {resident / 1e9:.1f} GB > 129 MB), no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single box"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": tag, "peak_kind": peak_kind,
+                     "step_frac": value * 1e6 / world * sum(STAGE_BYTES[args.precision]) / 1e9 / peak},
+        "stage_ms_per_launch": [stage_ms[0] / max(launches[0], 1), stage_ms[1] / max(launches[1], 1)],
+        "gpu_launches": 2 * args.steps,
+    }
+    with_extras = rank == 0 and world == 1 and not args.no_extras
+    if with_extras:
+        # end to end through the public API with host buffers: per step the
+        # state goes host -> device, one RK2 step (CFL dt) runs, the new state
+        # comes back device -> host (pinned host memory both ways)
+        ncell = box.ncell
+        dtype = torch.float32 if args.precision == "fp32" else torch.float64
+        cell_h = torch.from_numpy(box.cell.astype(np.float32 if args.precision == "fp32" else np.float64)).pin_memory()
+        face_h = [torch.from_numpy(f.astype(cell_h.numpy().dtype)).pin_memory() for f in box.face]
+        out_c = torch.empty_like(cell_h).pin_memory()
+        out_f = [torch.empty_like(f).pin_memory() for f in face_h]
+        nbytes = cell_h.numel() * cell_h.element_size() + sum(f.numel() * f.element_size() for f in face_h)
+        h = solver.h
+        mhd.mhd_set_state(h, [cell_h[v].data_ptr() for v in range(5)], [f.data_ptr() for f in face_h], 0)
+        mhd.mhd_step(h, -1.0, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            mhd.mhd_set_state(h, [cell_h[v].data_ptr() for v in range(5)], [f.data_ptr() for f in face_h], 0)
+            mhd.mhd_step(h, -1.0, 1)
+            mhd.mhd_get_state(h, [out_c[v].data_ptr() for v in range(5)], [f.data_ptr() for f in out_f], 0)
+        el = time.perf_counter() - t0
+        out["e2e"] = {"value": ncell * args.e2e_steps / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+        # plain FP64 path on the same GPU and the L1 error of this path against it
+        cmp = {}
+        dt = solver.cfl_dt()
+        ref = mhd.Solver(box, precision="fp64", stream=stream.cuda_stream)
+        ref.set_state(box.cell, box.face)
+        ref.step(dt, 1)
+        ref.set_state(box.cell, box.face)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ref.step_async(dt, args.compare_steps)
+        e1.record(stream)
+        stream.synchronize()
+        fp64_ms = e0.elapsed_time(e1) / args.compare_steps
+        ref.stats()
+        rc, rf = ref.get_state()
+        ref.close()
+        solver.set_state(box.cell, box.face)
+        solver.step(dt, args.compare_steps)
+        c, f = solver.get_state()
+        l1 = {}
+        names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz"]
+        for v in range(5):
+            l1[names[v]] = float(np.abs(c[v] - rc[v]).sum() / np.abs(rc[v]).sum())
+        bnorm = sum(float(np.abs(x).sum()) for x in rf)
+        for d in range(3):
+            l1[names[5 + d]] = float(np.abs(f[d] - rf[d]).sum() / max(np.abs(rf[d]).sum(), 1e-3 * bnorm))
+        cmp = {"fp64_value": box.ncell / (fp64_ms / 1e3) / 1e6, "unit": UNIT, "fp64_ms_per_step": fp64_ms,
+               "steps": args.compare_steps, "dt": dt, "l1_rel_vs_fp64": l1,
+               "note": "FP64 GPU path (parity with the FP64 oracle at 1e-12) as the reference"}
+        out["vs_fp64"] = cmp
+        out["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
+    elif rank == 0:
+        out["e2e"] = None
+    clocks = clk.summary()
+    out["clocks"] = clocks
+    solver.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * mhd_gb300.h -- C ABI of the GB300 (sm_103a) ideal-MHD Godunov hot path.
+ *
+ * The operation is the per-step update of the gPLUTO ideal-MHD method that the
+ * paper profiles (Sec. 2.2: reconstruction of primitive variables, Riemann
+ * solution at every interface, flux-conservative update, plus constrained
+ * transport for the magnetic field; Table 2 lists the matching kernels
+ * Reconstruct, HLLD_Solver, RightHandSide, CT_EMF and US).  The paper prints
+ * no formulas; the arithmetic follows the methods it names:
+ *   - primitive recovery p = (gamma-1)(E - |m|^2/(2 rho) - |B_c|^2/2), with the
+ *     cell field B_c the mean of the cell's two staggered faces;
+ *   - piecewise-linear reconstruction of (rho, v, p, B_t) with the MC limiter;
+ *   - the HLLD Riemann flux (Miyoshi & Kusano 2005) on every x, y and z face,
+ *     or HLL, or a learned per-face choice between the two;
+ *   - the flux divergence of (rho, m, E);
+ *   - edge EMFs by the upwind average of Gardiner & Stone (2005) and the
+ *     staggered update dB/dt = -curl E (div B stays at rounding);
+ *   - two-stage RK2 (Heun) with one dt per step;
+ *   - the CFL time step dt = cfl / max_cells sum_d (|v_d| + c_f,d)/Delta_d.
+ *
+ * Conventions
+ *   All pointers are plain host or device addresses; sizes are element counts.
+ *   Cell arrays (rho, mx, my, mz, E) hold nx*ny*nz values, x fastest:
+ *   index i + nx*(j + ny*k).  Face arrays hold the normal field component on
+ *   the faces of its own axis: Bx on x-faces (face i at x = i-1/2) with
+ *   nxf = nx + (bc[0] == MHD_BC_OUTFLOW) faces per row, index
+ *   i + nxf*(j + ny*k); By with nyf rows, index i + nx*(j + nyf*k); Bz with nzf
+ *   planes, index i + nx*(j + ny*k).  Periodic axes store n faces (face n is
+ *   face 0), outflow axes store n+1.
+ *   Element type: double for MHD_FP64 and MHD_MIXED, float for MHD_FP32.
+ *
+ * Ownership
+ *   A handle owns every device buffer it allocates; caller arrays are only
+ *   read or written during the call that receives them (copies in or out).
+ *   All work is enqueued on the CUDA stream given at creation (NULL = legacy
+ *   default stream).  Calls that return host values synchronise that stream.
+ *
+ * Errors
+ *   Every int-returning call returns MHD_OK (0) or a negative MHD_ERR_* code;
+ *   mhd_last_error() gives the text of the last failure on that handle.  No
+ *   call aborts or traps: device-side conditions (non-finite values, floor
+ *   hits, barrier timeouts) are recorded in a device status word and reported
+ *   by the next call that synchronises.
+ */
+#ifndef MHD_GB300_H
+#define MHD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MHD_OK 0
+#define MHD_ERR_INVALID (-1)   /* bad argument or configuration */
+#define MHD_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define MHD_ERR_NONFINITE (-3) /* a NaN or Inf state value was met on the device */
+#define MHD_ERR_TIMEOUT (-4)   /* a device-wide barrier gave up waiting */
+#define MHD_ERR_NOMEM (-5)     /* device allocation failed */
+
+#define MHD_BC_PERIODIC 0
+#define MHD_BC_OUTFLOW 1
+
+#define MHD_FP64 0   /* every step in FP64 */
+#define MHD_MIXED 1  /* FP32 reconstruction/Riemann/fluxes; FP64 pressure recovery,
+                        RK accumulation and div B */
+#define MHD_FP32 2   /* FP32 state and arithmetic */
+
+#define MHD_HLLD 0
+#define MHD_HLL 1
+#define MHD_LEARNED 2 /* per face: MLP predicts whether HLL suffices, else HLLD */
+
+#define MHD_EMF_UPWIND 0 /* Gardiner & Stone (2005) upwind contact average */
+#define MHD_EMF_MEAN 1   /* arithmetic mean of the four face EMFs (debug) */
+
+typedef struct {
+  int nx, ny, nz;          /* cells per axis (>= 1; >= 2 on an outflow axis) */
+  double dx, dy, dz;       /* cell sizes */
+  double gamma;            /* ratio of specific heats (5/3) */
+  double cfl;              /* Courant number for self-computed dt (0.4) */
+  int bc[3];               /* MHD_BC_* per axis */
+  int precision;           /* MHD_FP64 | MHD_MIXED | MHD_FP32 */
+  int riemann;             /* MHD_HLLD | MHD_HLL | MHD_LEARNED */
+  int emf;                 /* MHD_EMF_UPWIND | MHD_EMF_MEAN */
+  double rho_floor;        /* density floor used in primitive recovery (1e-10) */
+  double p_floor;          /* pressure floor (1e-10) */
+  int tile_x, tile_y, tile_z; /* tile of the fused stage kernel; 0 = default */
+} mhd_config;
+
+typedef struct {
+  long long rho_floor_hits; /* cell-stage evaluations that hit the density floor */
+  long long p_floor_hits;   /* ... the pressure floor */
+  long long faces_hll;      /* faces solved with HLL (MHD_LEARNED / MHD_HLL) */
+  long long faces_hlld;     /* faces solved with HLLD */
+  double last_dt;           /* dt of the last step taken */
+  int status;               /* device status word (bit 0 non-finite, bit 1 timeout) */
+  int steps;                /* steps taken since creation */
+} mhd_stats;
+
+typedef struct mhd_handle mhd_handle;
+
+/* Fill *cfg with defaults for an n = (nx, ny, nz) periodic box on [0,1]^3. */
+void mhd_default_config(mhd_config* cfg, int nx, int ny, int nz);
+
+/* Validate cfg, allocate the handle's device buffers (state, stage buffer,
+ * status words) and bind it to `cuda_stream` (a cudaStream_t, or NULL).
+ * Returns MHD_ERR_INVALID for a bad configuration, MHD_ERR_NOMEM when the
+ * device allocation fails.  *out is set only on success. */
+int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle** out);
+
+/* Copy a state in.  cell[0..4] = rho, mx, my, mz, E; face[0..2] = Bx, By, Bz
+ * in the layout above.  on_device = 1: the pointers are device addresses on
+ * the handle's device; 0: host addresses (pageable or pinned). */
+int mhd_set_state(mhd_handle* h, const void* const cell[5], const void* const face[3], int on_device);
+
+/* Copy the current state out (same layout and pointer kinds); synchronises. */
+int mhd_get_state(mhd_handle* h, void* cell[5], void* face[3], int on_device);
+
+/* Advance nsteps RK2 steps.  dt > 0: that dt for every step.  dt <= 0: each
+ * step takes the CFL dt of its own starting state, reduced on the device
+ * (no host round trip).  Enqueues 2 kernels per step; synchronises once at
+ * the end to read the status word. */
+int mhd_step(mhd_handle* h, double dt, int nsteps);
+
+/* Enqueue nsteps steps like mhd_step (dt <= 0: device-side CFL dt) without
+ * synchronising and without checking the status word (timing loops, CUDA-graph
+ * capture); the next synchronising call reports any device condition. */
+int mhd_step_async(mhd_handle* h, double dt, int nsteps);
+
+/* Profiling: on = 1 records CUDA events on the handle's stream around every
+ * stage-kernel launch, on = 0 stops.  mhd_get_profile synchronises and
+ * returns, per stage kernel (index 0: stage 1, 1: stage 2), the summed device
+ * time in ms and the number of launches recorded since the previous
+ * mhd_get_profile, then clears the record. */
+int mhd_set_profiling(mhd_handle* h, int on);
+int mhd_get_profile(mhd_handle* h, double ms[2], long long launches[2]);
+
+/* CFL dt of the current state (FP64 reduction on the device); synchronises. */
+int mhd_cfl_dt(mhd_handle* h, double* dt_out);
+
+/* max over cells of |div B| = |sum_d (B_d(i_d+1) - B_d(i_d)) / Delta_d|, FP64. */
+int mhd_divb_max(mhd_handle* h, double* out);
+
+/* Counters and the device status word; synchronises. */
+int mhd_get_stats(mhd_handle* h, mhd_stats* out);
+
+/* Free every resource of the handle (NULL is a no-op). */
+void mhd_destroy(mhd_handle* h);
+
+/* Text of the last failure on h (or of the last failed mhd_create when h is
+ * NULL).  The string lives until the next call on h. */
+const char* mhd_last_error(const mhd_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_GB300_H */

@@ -1,0 +1,265 @@
+"""ctypes binding of the C ABI in ``include/mhd_gb300.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libmhd_gb300.so``.  The functions keep the C names (``mhd_create``,
+``mhd_set_state``, ``mhd_step``, ...); :class:`Solver` is a thin owner of one
+handle that moves numpy arrays (host) or torch CUDA tensors (device) through
+those calls.  There is no CPU fallback: if the library is missing or cannot be
+loaded, importing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+MHD_OK = 0
+MHD_ERR_INVALID, MHD_ERR_CUDA, MHD_ERR_NONFINITE, MHD_ERR_TIMEOUT, MHD_ERR_NOMEM = -1, -2, -3, -4, -5
+MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
+MHD_FP64, MHD_MIXED, MHD_FP32 = 0, 1, 2
+MHD_HLLD, MHD_HLL, MHD_LEARNED = 0, 1, 2
+MHD_EMF_UPWIND, MHD_EMF_MEAN = 0, 1
+
+PRECISIONS = {"fp64": MHD_FP64, "mixed": MHD_MIXED, "fp32": MHD_FP32}
+RIEMANN = {"hlld": MHD_HLLD, "hll": MHD_HLL, "learned": MHD_LEARNED}
+
+
+class mhd_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("gamma", C.c_double), ("cfl", C.c_double),
+                ("bc", C.c_int * 3),
+                ("precision", C.c_int), ("riemann", C.c_int), ("emf", C.c_int),
+                ("rho_floor", C.c_double), ("p_floor", C.c_double),
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int)]
+
+
+class mhd_stats(C.Structure):
+    _fields_ = [("rho_floor_hits", C.c_longlong), ("p_floor_hits", C.c_longlong),
+                ("faces_hll", C.c_longlong), ("faces_hlld", C.c_longlong),
+                ("last_dt", C.c_double), ("status", C.c_int), ("steps", C.c_int)]
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_VP = C.c_void_p
+_H = C.c_void_p
+EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state", "mhd_step",
+           "mhd_step_async", "mhd_set_profiling", "mhd_get_profile", "mhd_cfl_dt", "mhd_divb_max",
+           "mhd_get_stats", "mhd_destroy", "mhd_last_error"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load (building first if the sources are newer) the CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+    L = C.CDLL(_build.LIB)
+    L.mhd_default_config.restype = None
+    L.mhd_default_config.argtypes = [C.POINTER(mhd_config), C.c_int, C.c_int, C.c_int]
+    L.mhd_create.restype = C.c_int
+    L.mhd_create.argtypes = [C.POINTER(mhd_config), _VP, C.POINTER(_H)]
+    L.mhd_set_state.restype = C.c_int
+    L.mhd_set_state.argtypes = [_H, _VP * 5, _VP * 3, C.c_int]
+    L.mhd_get_state.restype = C.c_int
+    L.mhd_get_state.argtypes = [_H, _VP * 5, _VP * 3, C.c_int]
+    L.mhd_step.restype = C.c_int
+    L.mhd_step.argtypes = [_H, C.c_double, C.c_int]
+    L.mhd_step_async.restype = C.c_int
+    L.mhd_step_async.argtypes = [_H, C.c_double, C.c_int]
+    L.mhd_set_profiling.restype = C.c_int
+    L.mhd_set_profiling.argtypes = [_H, C.c_int]
+    L.mhd_get_profile.restype = C.c_int
+    L.mhd_get_profile.argtypes = [_H, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.mhd_cfl_dt.restype = C.c_int
+    L.mhd_cfl_dt.argtypes = [_H, C.POINTER(C.c_double)]
+    L.mhd_divb_max.restype = C.c_int
+    L.mhd_divb_max.argtypes = [_H, C.POINTER(C.c_double)]
+    L.mhd_get_stats.restype = C.c_int
+    L.mhd_get_stats.argtypes = [_H, C.POINTER(mhd_stats)]
+    L.mhd_destroy.restype = None
+    L.mhd_destroy.argtypes = [_H]
+    L.mhd_last_error.restype = C.c_char_p
+    L.mhd_last_error.argtypes = [_H]
+    _lib = L
+    return L
+
+
+# ---- the C calls under their own names -------------------------------------
+
+def mhd_default_config(nx, ny, nz) -> mhd_config:
+    c = mhd_config()
+    load().mhd_default_config(C.byref(c), nx, ny, nz)
+    return c
+
+
+def _check(h, rc):
+    if rc != MHD_OK:
+        msg = load().mhd_last_error(h)
+        raise MHDError(rc, msg.decode() if msg else "")
+
+
+def mhd_create(cfg: mhd_config, stream=None):
+    h = _H()
+    rc = load().mhd_create(C.byref(cfg), _VP(stream or 0), C.byref(h))
+    _check(None, rc)
+    return h
+
+
+def mhd_set_state(h, cell_ptrs, face_ptrs, on_device: int):
+    _check(h, load().mhd_set_state(h, (_VP * 5)(*cell_ptrs), (_VP * 3)(*face_ptrs), on_device))
+
+
+def mhd_get_state(h, cell_ptrs, face_ptrs, on_device: int):
+    _check(h, load().mhd_get_state(h, (_VP * 5)(*cell_ptrs), (_VP * 3)(*face_ptrs), on_device))
+
+
+def mhd_step(h, dt: float, nsteps: int = 1):
+    _check(h, load().mhd_step(h, dt, nsteps))
+
+
+def mhd_step_async(h, dt: float, nsteps: int = 1):
+    _check(h, load().mhd_step_async(h, dt, nsteps))
+
+
+def mhd_set_profiling(h, on: bool):
+    _check(h, load().mhd_set_profiling(h, 1 if on else 0))
+
+
+def mhd_get_profile(h):
+    ms = (C.c_double * 2)()
+    n = (C.c_longlong * 2)()
+    _check(h, load().mhd_get_profile(h, ms, n))
+    return [ms[0], ms[1]], [n[0], n[1]]
+
+
+def mhd_cfl_dt(h) -> float:
+    out = C.c_double()
+    _check(h, load().mhd_cfl_dt(h, C.byref(out)))
+    return out.value
+
+
+def mhd_divb_max(h) -> float:
+    out = C.c_double()
+    _check(h, load().mhd_divb_max(h, C.byref(out)))
+    return out.value
+
+
+def mhd_get_stats(h) -> dict:
+    s = mhd_stats()
+    _check(h, load().mhd_get_stats(h, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in mhd_stats._fields_}
+
+
+def mhd_destroy(h):
+    if h:
+        load().mhd_destroy(h)
+
+
+def mhd_last_error(h=None) -> str:
+    m = load().mhd_last_error(h)
+    return m.decode() if m else ""
+
+
+# ---- convenience owner -----------------------------------------------------
+
+class Solver:
+    """One box on the GPU.  ``box`` is any object with nx, ny, nz, dx, dy, dz,
+    bc, gamma (and optionally cfl) -- e.g. ``inputs.Box``."""
+
+    def __init__(self, box, precision="fp64", riemann="hlld", emf="upwind", tile=(0, 0, 0),
+                 stream=None, cfl=None, rho_floor=1e-10, p_floor=1e-10):
+        c = mhd_default_config(box.nx, box.ny, box.nz)
+        c.dx, c.dy, c.dz = box.dx, box.dy, box.dz
+        c.gamma = box.gamma
+        c.cfl = cfl if cfl is not None else getattr(box, "cfl", 0.4)
+        c.bc = (C.c_int * 3)(*box.bc)
+        c.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        c.riemann = RIEMANN[riemann] if isinstance(riemann, str) else riemann
+        c.emf = MHD_EMF_MEAN if emf == "mean" else MHD_EMF_UPWIND
+        c.rho_floor, c.p_floor = rho_floor, p_floor
+        c.tile_x, c.tile_y, c.tile_z = tile
+        self.cfg = c
+        self.dims = (box.nx, box.ny, box.nz)
+        self.bc = tuple(box.bc)
+        self.dtype = np.float32 if c.precision == MHD_FP32 else np.float64
+        self.h = mhd_create(c, stream)
+
+    def face_shapes(self):
+        nx, ny, nz = self.dims
+        o = [1 if b == MHD_BC_OUTFLOW else 0 for b in self.bc]
+        return [(nz, ny, nx + o[0]), (nz, ny + o[1], nx), (nz + o[2], ny, nx)]
+
+    def set_state(self, cell, face):
+        """Host numpy arrays (converted to the handle's element type) or torch
+        CUDA tensors of that type."""
+        if hasattr(cell, "data_ptr") and getattr(cell, "is_cuda", False):
+            cp = [cell[v].data_ptr() for v in range(5)]
+            fp = [f.data_ptr() for f in face]
+            for t in [cell] + list(face):
+                assert t.is_contiguous()
+            mhd_set_state(self.h, cp, fp, 1)
+            return
+        self._keep = [np.ascontiguousarray(cell, dtype=self.dtype)] + \
+                     [np.ascontiguousarray(f, dtype=self.dtype) for f in face]
+        c = self._keep[0]
+        assert c.shape == (5,) + self.dims[::-1], c.shape
+        for f, s in zip(self._keep[1:], self.face_shapes()):
+            assert f.shape == s, (f.shape, s)
+        mhd_set_state(self.h, [c[v].ctypes.data for v in range(5)], [f.ctypes.data for f in self._keep[1:]], 0)
+
+    def get_state(self):
+        cell = np.empty((5,) + self.dims[::-1], dtype=self.dtype)
+        face = [np.empty(s, dtype=self.dtype) for s in self.face_shapes()]
+        mhd_get_state(self.h, [cell[v].ctypes.data for v in range(5)], [f.ctypes.data for f in face], 0)
+        return cell, face
+
+    def step(self, dt: float, nsteps: int = 1):
+        mhd_step(self.h, dt, nsteps)
+
+    def step_async(self, dt: float, nsteps: int = 1):
+        mhd_step_async(self.h, dt, nsteps)
+
+    def cfl_dt(self) -> float:
+        return mhd_cfl_dt(self.h)
+
+    def set_profiling(self, on: bool):
+        mhd_set_profiling(self.h, on)
+
+    def profile(self):
+        """(ms per stage kernel, launches per stage kernel) since the last call."""
+        return mhd_get_profile(self.h)
+
+    def divb_max(self) -> float:
+        return mhd_divb_max(self.h)
+
+    def stats(self) -> dict:
+        return mhd_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,34 @@
+"""Shared helpers of the test suite (error metrics, oracle configs)."""
+import numpy as np
+
+import oracle as O
+
+
+def ocfg(b, **kw):
+    return O.Config(b.nx, b.ny, b.nz, b.dx, b.dy, b.dz, b.gamma, getattr(b, "cfl", 0.4), tuple(b.bc), **kw)
+
+
+def rel_l1(q, ref, floor=0.0):
+    """Relative L1 error sum|q - ref| / max(sum|ref|, floor); with a zero
+    denominator, the mean absolute error instead."""
+    q = np.asarray(q, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = max(float(np.abs(ref).sum()), floor)
+    num = float(np.abs(q - ref).sum())
+    return num / den if den > 0 else num / max(ref.size, 1)
+
+
+def state_errors(cell, face, ref_cell, ref_face):
+    """Per-variable relative L1 errors.  A vector component is measured
+    against max(its own L1 norm, 1e-3 x the L1 norm of the whole vector), so a
+    component that is zero up to rounding (v_z, B_z of a 2D problem) is not
+    divided by its own rounding noise."""
+    names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz"]
+    mnorm = float(np.abs(np.asarray(ref_cell[1:4], dtype=np.float64)).sum())
+    bnorm = float(sum(np.abs(np.asarray(f, dtype=np.float64)).sum() for f in ref_face))
+    errs = {}
+    for v in range(5):
+        errs[names[v]] = rel_l1(cell[v], ref_cell[v], 1e-3 * mnorm if 1 <= v <= 3 else 0.0)
+    for d in range(3):
+        errs[names[5 + d]] = rel_l1(face[d], ref_face[d], 1e-3 * bnorm)
+    return errs

@@ -1,0 +1,68 @@
+"""The C-ABI library loads, exports every symbol the header declares, and
+rejects bad configurations on the host (no GPU needed: validation runs before
+any CUDA call)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2606_12753_gb300 import mhd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = mhd.load()
+    names = declared_functions()
+    assert "mhd_create" in names and "mhd_step" in names
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    for n in mhd.EXPORTS:
+        assert n in names
+
+
+def test_default_config_host_only():
+    c = mhd.mhd_default_config(32, 16, 8)
+    assert (c.nx, c.ny, c.nz) == (32, 16, 8)
+    assert c.gamma == pytest.approx(5 / 3) and c.cfl == pytest.approx(0.4)
+    assert c.dx == pytest.approx(1 / 32)
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("gamma", 1.0), ("cfl", 0.0), ("precision", 7),
+                                         ("riemann", 9), ("emf", 3), ("rho_floor", 0.0), ("tile_x", 65),
+                                         ("tile_y", -1)])
+def test_invalid_config_rejected(field, value):
+    c = mhd.mhd_default_config(16, 16, 16)
+    setattr(c, field, value)
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert ei.value.code == mhd.MHD_ERR_INVALID
+    assert mhd.mhd_last_error(None)
+
+
+def test_outflow_axis_needs_two_cells():
+    c = mhd.mhd_default_config(1, 16, 16)
+    c.bc = (C.c_int * 3)(1, 0, 0)
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert ei.value.code == mhd.MHD_ERR_INVALID
+
+
+def test_tile_smem_limit():
+    c = mhd.mhd_default_config(64, 64, 64)
+    c.tile_x, c.tile_y = 64, 64
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert "shared memory" in str(ei.value)
