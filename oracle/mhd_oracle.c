@@ -23,8 +23,9 @@
  *            HLL (Harten, Lax & van Leer 1983) as the cheap alternative.
  *   step 4   flux divergence of the 5 hydrodynamic variables (x, y, z order).
  *   step 5   constrained-transport edge EMFs: upwind "contact" average of
- *            Gardiner & Stone 2005 (JCP 205:509, their eqs. 41-50), or the
- *            arithmetic mean of the 4 face EMFs as a debug option.
+ *            Gardiner & Stone 2005 (JCP 205:509, their eqs. 41-50), oriented
+ *            by the sign of the face mass flux with a rounding deadband, or
+ *            the arithmetic mean of the 4 face EMFs as a debug option.
  *   step 6   face-B update dB/dt = -curl E on the staggered faces.
  *   step 7   two-stage RK2 (Heun): U* = U + dt L(U);
  *            U^{n+1} = (U + U* + dt L(U*))/2.
@@ -368,8 +369,12 @@ static void rotated(const grid *g, double *W[8], int d, size_t q, double *w) {
 
 /* face fluxes along d for every face whose 4-cell stencil lies in the
  * extended grid.  F[q] (q = 0..6, rotated order) is stored at the (N+1)^3
- * lattice index of the face's right cell (face I = left face of cell I). */
-static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7]) {
+ * lattice index of the face's right cell (face I = left face of cell I).
+ * M holds the mass flux that orients the upwind EMF average: F[0] itself,
+ * or exactly 0 when |F[0]| <= 1e-10 (rho_L + rho_R)/2 max(c_fL, c_fR), so a
+ * mass flux that vanishes up to rounding takes the mean of both sides
+ * (reading of the tie rule, which the method leaves open). */
+static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7], double *M) {
   const orc_cfg *c = g->c;
   int lo[3] = {0, 0, 0}, hi[3] = {g->N[0], g->N[1], g->N[2]};
   lo[d] = 2;
@@ -410,6 +415,9 @@ static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7
         else orc_hlld(wl, wr, bn, c->gamma, f);
         size_t fq = fidx(g, I, J, K);
         for (int v = 0; v < 7; ++v) F[v][fq] = f[v];
+        double cl = orc_fast_speed(wl, bn, c->gamma), cr = orc_fast_speed(wr, bn, c->gamma);
+        double band = 1e-10 * 0.5 * (wl[0] + wr[0]) * (cl > cr ? cl : cr);
+        M[fq] = fabs(f[0]) <= band ? 0.0 : f[0];
       }
 }
 
@@ -435,16 +443,17 @@ static void spatial_operator(const orc_cfg *c, double *const cell[5], double *co
   g.ncell = (size_t)g.N[0] * g.N[1] * g.N[2];
   g.nedge = (size_t)(g.N[0] + 1) * (g.N[1] + 1) * (g.N[2] + 1);
 
-  double *W[8], *Bf[3], *F[3][7], *Ec[3], *Ed[3];
+  double *W[8], *Bf[3], *F[3][7], *M[3], *Ec[3], *Ed[3];
   for (int v = 0; v < 8; ++v) W[v] = calloc(g.ncell, sizeof(double));
   for (int d = 0; d < 3; ++d) {
     Bf[d] = calloc(g.nedge, sizeof(double));
     Ec[d] = calloc(g.ncell, sizeof(double));
     Ed[d] = calloc(g.nedge, sizeof(double));
+    M[d] = calloc(g.nedge, sizeof(double));
     for (int v = 0; v < 7; ++v) F[d][v] = calloc(g.nedge, sizeof(double));
   }
   build_primitives(&g, cell, face, W, Bf, st);
-  for (int d = 0; d < 3; ++d) sweep(&g, W, Bf, d, F[d]);
+  for (int d = 0; d < 3; ++d) sweep(&g, W, Bf, d, F[d], M[d]);
 
   /* cell-centred reference EMF E_c = -v x B_c */
   for (size_t q = 0; q < g.ncell; ++q) {
@@ -474,13 +483,13 @@ static void spatial_operator(const orc_cfg *c, double *const cell[5], double *co
           /* a-faces at (a-1/2, b-1) and (a-1/2, b); t1 of an a-sweep is b */
           double fa_m = -F[a][5][fidx(&g, Pbm[0], Pbm[1], Pbm[2])];
           double fa_p = -F[a][5][fidx(&g, P[0], P[1], P[2])];
-          double ma_m = F[a][0][fidx(&g, Pbm[0], Pbm[1], Pbm[2])];
-          double ma_p = F[a][0][fidx(&g, P[0], P[1], P[2])];
+          double ma_m = M[a][fidx(&g, Pbm[0], Pbm[1], Pbm[2])];
+          double ma_p = M[a][fidx(&g, P[0], P[1], P[2])];
           /* b-faces at (a-1, b-1/2) and (a, b-1/2); t2 of a b-sweep is a */
           double fb_m = F[b][6][fidx(&g, Pam[0], Pam[1], Pam[2])];
           double fb_p = F[b][6][fidx(&g, P[0], P[1], P[2])];
-          double mb_m = F[b][0][fidx(&g, Pam[0], Pam[1], Pam[2])];
-          double mb_p = F[b][0][fidx(&g, P[0], P[1], P[2])];
+          double mb_m = M[b][fidx(&g, Pam[0], Pam[1], Pam[2])];
+          double mb_p = M[b][fidx(&g, P[0], P[1], P[2])];
           /* cell-centred values: (a-1,b-1), (a,b-1), (a-1,b), (a,b) */
           double e_mm = Ec[cdir][cidx(&g, Pabm[0], Pabm[1], Pabm[2])];
           double e_pm = Ec[cdir][cidx(&g, Pbm[0], Pbm[1], Pbm[2])];
@@ -555,6 +564,7 @@ static void spatial_operator(const orc_cfg *c, double *const cell[5], double *co
     free(Bf[d]);
     free(Ec[d]);
     free(Ed[d]);
+    free(M[d]);
     for (int v = 0; v < 7; ++v) free(F[d][v]);
   }
 }

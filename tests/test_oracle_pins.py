@@ -296,3 +296,19 @@ def test_checkpoint_resume_bitwise():
     np.testing.assert_array_equal(c1, cb)
     for d in range(3):
         np.testing.assert_array_equal(f1[d], fb[d])
+
+
+def test_step_is_well_conditioned_on_a_low_beta_blast():
+    """A 1e-15 relative perturbation of the state moves one RK2 step of a
+    low-beta blast by rounding only.  Without the deadband on the mass-flux
+    sign that orients the upwind EMF average, rounding-level mass fluxes flip
+    the upwind side and the face field jumps by O(v B)."""
+    box = I.blast_batch(1, seed=3, nmin=24, nmax=32)[0]
+    cfg = cfg_of(box)
+    rng = np.random.default_rng(0)
+    c0, f0, _ = O.step(cfg, box.cell, box.face, 5e-4, nsteps=2)
+    cell = box.cell * (1 + 1e-15 * rng.standard_normal(box.cell.shape))
+    c1, f1, _ = O.step(cfg, cell, box.face, 5e-4, nsteps=2)
+    from helpers import state_errors
+    errs = state_errors(c1, f1, c0, f0)
+    assert max(errs.values()) < 1e-11, errs
