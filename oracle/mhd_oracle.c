@@ -18,7 +18,8 @@
  *            p = (gamma-1)(E - |m|^2/(2 rho) - |B|^2/2), with floors.
  *   step 2   piecewise-linear reconstruction of the 7 primitives (rho, v_n,
  *            v_t1, v_t2, p, B_t1, B_t2) with the monotonised-central (MC)
- *            limiter (van Leer 1977), one direction at a time.
+ *            limiter (van Leer 1977), one direction at a time; face values
+ *            of rho and p floored.
  *   step 3   HLLD Riemann flux (Miyoshi & Kusano 2005, JCP 208:315) per face;
  *            HLL (Harten, Lax & van Leer 1983) as the cheap alternative.
  *   step 4   flux divergence of the 5 hydrodynamic variables (x, y, z order).
@@ -31,9 +32,10 @@
  *            U^{n+1} = (U + U* + dt L(U*))/2.
  *   CFL      dt = C / max_cells sum_{d: n_d>1} (|v_d| + c_f,d)/Delta_d.
  *
- * Boundaries: periodic (wrap) or outflow (zero-gradient: ghost cells copy the
- * nearest interior cell, tangential ghost faces are copied, the ghost normal
- * face is extrapolated linearly so that div B = 0 in every ghost cell).
+ * Boundaries: periodic (wrap) or outflow (zero-gradient: ghost cells copy rho,
+ * v and p of the nearest interior cell, tangential ghost faces are copied, the
+ * ghost normal face is extrapolated linearly so that div B = 0 in every ghost
+ * cell, and the ghost cell-centred field is the mean of its faces).
  * Three ghost layers are filled explicitly; nothing here is fused.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
@@ -305,7 +307,11 @@ static double face_value(const grid *g, double *const face[3], int d, int ijk[3]
 
 /* W: 8 primitive arrays on extended cells (rho, vx, vy, vz, p, Bcx, Bcy, Bcz)
  * Bf: 3 face arrays on the extended (N+1)^3 lattice (face index I = left face
- * of extended cell I). */
+ * of extended cell I).  A ghost cell takes rho, v and p of the interior cell
+ * it maps to (periodic wrap or outflow clamp), and its cell-centred field
+ * from its own (ghost) faces: on an outflow axis the ghost normal field is the
+ * linear extrapolation, so B_c there differs from the interior cell's while
+ * the primitives rho, v, p are copied (zero gradient). */
 static void build_primitives(const grid *g, double *const cell[5], double *const face[3],
                              double *W[8], double *Bf[3], orc_stats *st) {
   const orc_cfg *c = g->c;
@@ -318,6 +324,35 @@ static void build_primitives(const grid *g, double *const cell[5], double *const
           Bf[d][fidx(g, I, J, K)] = face_value(g, face, d, a);
         }
       }
+  /* primitives of the interior cells, from each cell's own faces */
+  size_t nin = (size_t)g->n[0] * g->n[1] * g->n[2];
+  double *Wi[5];
+  for (int v = 0; v < 5; ++v) Wi[v] = malloc(nin * sizeof(double));
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) {
+        size_t s = (size_t)i + (size_t)g->n[0] * ((size_t)j + (size_t)g->n[1] * (size_t)k);
+        int I = i + NG, J = j + NG, K = k + NG;
+        double rho = cell[0][s], mx = cell[1][s], my = cell[2][s], mz = cell[3][s], e = cell[4][s];
+        double bx = 0.5 * (Bf[0][fidx(g, I, J, K)] + Bf[0][fidx(g, I + 1, J, K)]);
+        double by = 0.5 * (Bf[1][fidx(g, I, J, K)] + Bf[1][fidx(g, I, J + 1, K)]);
+        double bz = 0.5 * (Bf[2][fidx(g, I, J, K)] + Bf[2][fidx(g, I, J, K + 1)]);
+        if (rho < c->rho_floor) {
+          rho = c->rho_floor;
+          if (st) st->rho_floor_hits++;
+        }
+        double p = (c->gamma - 1.0) *
+                   (e - 0.5 * (mx * mx + my * my + mz * mz) / rho - 0.5 * (bx * bx + by * by + bz * bz));
+        if (p < c->p_floor) {
+          p = c->p_floor;
+          if (st) st->p_floor_hits++;
+        }
+        Wi[0][s] = rho;
+        Wi[1][s] = mx / rho;
+        Wi[2][s] = my / rho;
+        Wi[3][s] = mz / rho;
+        Wi[4][s] = p;
+      }
   for (int K = 0; K < g->N[2]; ++K)
     for (int J = 0; J < g->N[1]; ++J)
       for (int I = 0; I < g->N[0]; ++I) {
@@ -325,32 +360,13 @@ static void build_primitives(const grid *g, double *const cell[5], double *const
         int j = wrap_or_clamp(J - NG, g->n[1], c->bc[1]);
         int k = wrap_or_clamp(K - NG, g->n[2], c->bc[2]);
         size_t s = (size_t)i + (size_t)g->n[0] * ((size_t)j + (size_t)g->n[1] * (size_t)k);
-        double rho = cell[0][s], mx = cell[1][s], my = cell[2][s], mz = cell[3][s], e = cell[4][s];
-        double bx = 0.5 * (Bf[0][fidx(g, I, J, K)] + Bf[0][fidx(g, I + 1, J, K)]);
-        double by = 0.5 * (Bf[1][fidx(g, I, J, K)] + Bf[1][fidx(g, I, J + 1, K)]);
-        double bz = 0.5 * (Bf[2][fidx(g, I, J, K)] + Bf[2][fidx(g, I, J, K + 1)]);
-        int interior = I >= NG && I < NG + g->n[0] && J >= NG && J < NG + g->n[1] &&
-                       K >= NG && K < NG + g->n[2];
-        if (rho < c->rho_floor) {
-          rho = c->rho_floor;
-          if (interior && st) st->rho_floor_hits++;
-        }
-        double p = (c->gamma - 1.0) *
-                   (e - 0.5 * (mx * mx + my * my + mz * mz) / rho - 0.5 * (bx * bx + by * by + bz * bz));
-        if (p < c->p_floor) {
-          p = c->p_floor;
-          if (interior && st) st->p_floor_hits++;
-        }
         size_t q = cidx(g, I, J, K);
-        W[0][q] = rho;
-        W[1][q] = mx / rho;
-        W[2][q] = my / rho;
-        W[3][q] = mz / rho;
-        W[4][q] = p;
-        W[5][q] = bx;
-        W[6][q] = by;
-        W[7][q] = bz;
+        for (int v = 0; v < 5; ++v) W[v][q] = Wi[v][s];
+        W[5][q] = 0.5 * (Bf[0][fidx(g, I, J, K)] + Bf[0][fidx(g, I + 1, J, K)]);
+        W[6][q] = 0.5 * (Bf[1][fidx(g, I, J, K)] + Bf[1][fidx(g, I, J + 1, K)]);
+        W[7][q] = 0.5 * (Bf[2][fidx(g, I, J, K)] + Bf[2][fidx(g, I, J, K + 1)]);
       }
+  for (int v = 0; v < 5; ++v) free(Wi[v]);
 }
 
 /* rotated order of the primitives for a sweep along d:
@@ -397,18 +413,17 @@ static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7
           sL[v] = orc_mc_slope(wm2[v], wm1[v], w0[v]);
           sR[v] = orc_mc_slope(wm1[v], w0[v], wp1[v]);
         }
-        /* positivity: a cell whose reconstructed face values of rho or p
-         * would be <= 0 uses zero slopes in this direction */
-        if (wm1[0] - 0.5 * sL[0] <= 0.0 || wm1[0] + 0.5 * sL[0] <= 0.0 ||
-            wm1[4] - 0.5 * sL[4] <= 0.0 || wm1[4] + 0.5 * sL[4] <= 0.0)
-          for (int v = 0; v < 7; ++v) sL[v] = 0.0;
-        if (w0[0] - 0.5 * sR[0] <= 0.0 || w0[0] + 0.5 * sR[0] <= 0.0 ||
-            w0[4] - 0.5 * sR[4] <= 0.0 || w0[4] + 0.5 * sR[4] <= 0.0)
-          for (int v = 0; v < 7; ++v) sR[v] = 0.0;
         for (int v = 0; v < 7; ++v) {
           wl[v] = wm1[v] + 0.5 * sL[v];
           wr[v] = w0[v] - 0.5 * sR[v];
         }
+        /* positivity: face values of rho and p are floored.  The MC slope
+         * keeps a face value between the neighbouring cell values, which are
+         * floored already, so this only absorbs rounding. */
+        if (wl[0] < c->rho_floor) wl[0] = c->rho_floor;
+        if (wr[0] < c->rho_floor) wr[0] = c->rho_floor;
+        if (wl[4] < c->p_floor) wl[4] = c->p_floor;
+        if (wr[4] < c->p_floor) wr[4] = c->p_floor;
         double bn = Bf[d][fidx(g, I, J, K)];
         double f[7];
         if (c->riemann == ORC_HLL) orc_hll(wl, wr, bn, c->gamma, f);
