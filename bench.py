@@ -6,9 +6,9 @@ turbulence box, 256^3 periodic, mixed FP32/FP64 precision.
 One "step" is one full RK2 step (both fused stage kernels, with the CFL
 max-reduction fused into stage 1 and the self-computed dt used by stage 2)
 over the whole box.  Inputs are generated from the seeded turbulence recipe
-(synthetic; the paper's runs use no dataset).  The state (2.7 GB with the
-stage buffer) is far larger than the 129 MB L2, so no flush is needed between
-steps.
+(synthetic; the paper's runs use no dataset).  The resident buffers (4.1 GB:
+state, stage increment, primitives) are far larger than the 129 MB L2, so no
+flush is needed between steps.
 
 Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
 oracle instead (on a bounded sample of the same workload).
@@ -31,8 +31,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-updates/s on 1 GB300 at 256^3 MHD; % HBM roofline; vs plain FP64 at L1 error"
 UNIT = "Mcell-updates/s"
-# algorithmic HBM bytes per cell per stage kernel launch (read + write, fully fused)
-STAGE_BYTES = {"fp64": (128, 192), "mixed": (96, 160), "fp32": (64, 96)}
+# algorithmic HBM bytes per cell per stage-kernel launch: stage 1 reads the
+# primitives W (11 arrays) and U^n (8), writes K1 (8) and W(U*); stage 2 reads
+# W(U*), U^n and K1, writes U^{n+1} and W(U^{n+1})
+STAGE_BYTES = {"fp64": (304, 368), "mixed": (184, 248), "fp32": (152, 184)}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -251,7 +253,7 @@ def run_ours(args):
     traffic, src = traffic_from_profiles(tag)
     elem = 4 if args.precision == "fp32" else 8
     kelem = 8 if args.precision == "fp64" else 4
-    resident = box.ncell * 8 * (2 * elem + kelem)
+    resident = box.ncell * (8 * (2 * elem + kelem) + 2 * 11 * kelem)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,

@@ -135,6 +135,13 @@ int mhd_step_async(mhd_handle* h, double dt, int nsteps);
 int mhd_set_profiling(mhd_handle* h, int on);
 int mhd_get_profile(mhd_handle* h, double ms[2], long long launches[2]);
 
+/* Evaluate the spatial operator L(U) of the current state (one stage-1 pass:
+ * reconstruction, Riemann fluxes, flux divergence, edge EMFs, -curl E) and
+ * copy it out in the state layout: dU/dt for the 5 cell arrays and dB/dt for
+ * the 3 face arrays.  Element type: double for MHD_FP64, float for MHD_MIXED
+ * and MHD_FP32.  The state is unchanged; synchronises. */
+int mhd_rhs(mhd_handle* h, void* cell[5], void* face[3], int on_device);
+
 /* CFL dt of the current state (FP64 reduction on the device); synchronises. */
 int mhd_cfl_dt(mhd_handle* h, double* dt_out);
 

@@ -25,15 +25,15 @@ template <typename R> struct Eps;
 template <> struct Eps<double> { static constexpr double degen = 1e-12; };
 template <> struct Eps<float> { static constexpr float degen = 1e-6f; };
 
-template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
-template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
-template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
-__device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+template <typename R> __host__ __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+template <typename R> __host__ __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+template <typename R> __host__ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+__host__ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+__host__ __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 
 // MC-limited slope of the middle of three values.
 template <typename R>
-__device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
+__host__ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
   R dm = q0 - qm, dp = qp - q0;
   R a = R(2) * rabs(dm), b = R(2) * rabs(dp), c = R(0.5) * rabs(dm + dp);
   R m = rmin(rmin(a, b), c);
@@ -43,7 +43,7 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
 
 // Fast magnetosonic speed along the normal; w = (rho, vn, vt1, vt2, p, Bt1, Bt2).
 template <typename R>
-__device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
+__host__ __device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
   R rinv = R(1) / w[0];
   R a2 = gamma * w[4] * rinv;
   R b2 = (bn * bn + w[5] * w[5] + w[6] * w[6]) * rinv;
@@ -55,7 +55,7 @@ __device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
 
 // Physical flux along the normal (7 components, rotated order).
 template <typename R>
-__device__ __forceinline__ void phys_flux(const R* w, R bn, R gamma, R* f) {
+__host__ __device__ __forceinline__ void phys_flux(const R* w, R bn, R gamma, R* f) {
   R rho = w[0], u = w[1], v = w[2], ww = w[3], p = w[4], by = w[5], bz = w[6];
   R b2 = bn * bn + by * by + bz * bz;
   R pt = p + R(0.5) * b2;
@@ -72,16 +72,17 @@ __device__ __forceinline__ void phys_flux(const R* w, R bn, R gamma, R* f) {
 }
 
 template <typename R>
-__device__ __forceinline__ R total_energy(const R* w, R bn, R gamma) {
+__host__ __device__ __forceinline__ R total_energy(const R* w, R bn, R gamma) {
   return w[4] / (gamma - R(1)) + R(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
          R(0.5) * (bn * bn + w[5] * w[5] + w[6] * w[6]);
 }
 
 // HLL flux.
 template <typename R>
-__device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn, R gamma, R* f) {
+__host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn, R gamma, R* f, R* cmax = nullptr) {
   R cl = fast_speed(wl, bn, gamma), cr = fast_speed(wr, bn, gamma);
   R cm = rmax(cl, cr);
+  if (cmax) *cmax = cm;
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
   if (sl >= R(0)) { phys_flux(wl, bn, gamma, f); return; }
@@ -103,7 +104,7 @@ struct Star {
 };
 
 template <typename R>
-__device__ __forceinline__ Star<R> star_side(const R* w, R bn, R gamma, R s, R sm, R pts) {
+__host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R gamma, R s, R sm, R pts) {
   Star<R> st;
   R rho = w[0], u = w[1], v = w[2], ww = w[3], by = w[5], bz = w[6];
   R sd = s - u;
@@ -137,9 +138,10 @@ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R gamma, R s, R s
 // L, L*, L**, R**, R*, R; sign(0) = 0; degenerate star states (den ~ 0)
 // keep the outer tangential values.
 template <typename R>
-__device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R bn, R gamma, R* f) {
+__host__ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R bn, R gamma, R* f, R* cmax = nullptr) {
   R cl = fast_speed(wl, bn, gamma), cr = fast_speed(wr, bn, gamma);
   R cm = rmax(cl, cr);
+  if (cmax) *cmax = cm;
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
   if (sl > R(0)) { phys_flux(wl, bn, gamma, f); return; }
@@ -181,9 +183,18 @@ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R bn, R gamm
   }
 }
 
+// Mass flux that orients the upwind EMF average: the face mass flux, or 0
+// when it lies inside a rounding deadband eps (rho_L + rho_R)/2 c_max, so
+// rounding noise of a vanishing mass flux selects the mean of both sides
+// instead of an arbitrary side.
+template <typename R>
+__host__ __device__ __forceinline__ R oriented_mass_flux(R f0, R rho_l, R rho_r, R cmax, R eps) {
+  return rabs(f0) <= eps * R(0.5) * (rho_l + rho_r) * cmax ? R(0) : f0;
+}
+
 // Gardiner-Stone upwind selection by the sign of a face mass flux.
 template <typename R>
-__device__ __forceinline__ R upwind(R m, R lo, R hi) {
+__host__ __device__ __forceinline__ R upwind(R m, R lo, R hi) {
   return m > R(0) ? lo : (m < R(0) ? hi : R(0.5) * (lo + hi));
 }
 
@@ -192,7 +203,7 @@ __device__ __forceinline__ R upwind(R m, R lo, R hi) {
 // a-1, fb_p at a), the face mass fluxes, and the four cell-centred values
 // e_mm (a-1,b-1), e_pm (a,b-1), e_mp (a-1,b), e_pp (a,b).
 template <typename R>
-__device__ __forceinline__ R edge_emf(R fa_m, R fa_p, R ma_m, R ma_p, R fb_m, R fb_p, R mb_m, R mb_p,
+__host__ __device__ __forceinline__ R edge_emf(R fa_m, R fa_p, R ma_m, R ma_p, R fb_m, R fb_p, R mb_m, R mb_p,
                                       R e_mm, R e_pm, R e_mp, R e_pp, bool plain_mean) {
   R avg = R(0.25) * (fa_m + fa_p + fb_m + fb_p);
   if (plain_mean) return avg;
@@ -204,24 +215,21 @@ __device__ __forceinline__ R edge_emf(R fa_m, R fa_p, R ma_m, R ma_p, R fb_m, R 
 }
 
 // Reconstruct the two states of a face from four cells along the normal
-// (c0, c1 | c2, c3), 7 rotated primitives each.  A cell whose face values of
-// rho or p would not be positive uses zero slopes.
+// (c0, c1 | c2, c3), 7 rotated primitives each; face values of rho and p are
+// floored (MC keeps them between the neighbouring cell values, so the floor
+// only absorbs rounding next to a cell that sits at the floor).
 template <typename R>
-__device__ __forceinline__ void plm_face(const R* c0, const R* c1, const R* c2, const R* c3, R* wl, R* wr) {
-  R sl[7], sr[7];
+__host__ __device__ __forceinline__ void plm_face(const R* c0, const R* c1, const R* c2, const R* c3, R* wl, R* wr,
+                                                  R rho_floor, R p_floor) {
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    sl[q] = mc_slope(c0[q], c1[q], c2[q]);
-    sr[q] = mc_slope(c1[q], c2[q], c3[q]);
+    wl[q] = c1[q] + R(0.5) * mc_slope(c0[q], c1[q], c2[q]);
+    wr[q] = c2[q] - R(0.5) * mc_slope(c1[q], c2[q], c3[q]);
   }
-  R hl0 = R(0.5) * sl[0], hl4 = R(0.5) * sl[4], hr0 = R(0.5) * sr[0], hr4 = R(0.5) * sr[4];
-  bool badl = (c1[0] - hl0 <= R(0)) | (c1[0] + hl0 <= R(0)) | (c1[4] - hl4 <= R(0)) | (c1[4] + hl4 <= R(0));
-  bool badr = (c2[0] - hr0 <= R(0)) | (c2[0] + hr0 <= R(0)) | (c2[4] - hr4 <= R(0)) | (c2[4] + hr4 <= R(0));
-#pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    wl[q] = c1[q] + (badl ? R(0) : R(0.5) * sl[q]);
-    wr[q] = c2[q] - (badr ? R(0) : R(0.5) * sr[q]);
-  }
+  wl[0] = rmax(wl[0], rho_floor);
+  wr[0] = rmax(wr[0], rho_floor);
+  wl[4] = rmax(wl[4], p_floor);
+  wr[4] = rmax(wr[4], p_floor);
 }
 
 }  // namespace mhd

@@ -1,20 +1,20 @@
-// Fused RK2 stage kernel of the ideal-MHD Godunov step on GB300 (sm_103a).
+// Shared definitions of the fused RK2 stage kernels (ideal MHD, GB300 sm_103a).
 //
-// One CTA owns a TX x TY column of cells and marches along z through a chunk
-// of TZ planes.  Per output plane k it
-//   A  loads plane k+2 (tile + 2-cell halo), recovers primitives into a
-//      4-plane shared-memory ring (periodic wrap / outflow clamp by index),
-//   B  solves the Riemann problem (HLLD, HLL or the learned choice) on the
-//      z-faces k+1/2 and on the x- and y-faces of plane k+1 (one halo row
-//      across, for the edge EMFs), and forms the cell-centred EMF -v x B,
-//   C  accumulates the flux divergence, builds the Gardiner-Stone edge EMFs
-//      E_z(plane k), E_x and E_y (k+1/2),
-//   D  writes plane k: stage 1 stores L(U^n) (5 cell + 3 face increments)
-//      and folds the CFL speed into a per-CTA max; stage 2 writes
-//      U^{n+1} = U^n + dt/2 (L(U^n) + L(U*)) with U* = U^n + dt L(U^n)
-//      rebuilt on the fly from the stage-1 buffer.
-// This is the paper's chain Reconstruct -> HLLD_Solver -> RightHandSide ->
-// CT_EMF -> US (Sec. 2.2, Table 2) fused into one pass over HBM per stage.
+// Data kept in HBM per box (SoA, x fastest, one packed allocation each):
+//   U[2]  conserved state, ping-pong (rho, mx, my, mz, E | Bx, By, Bz faces),
+//         element type S (double for FP64 and mixed, float for FP32);
+//   K1    stage-1 increments L(U^n), element type K (double / float / float);
+//   W[2]  primitives of a state, 11 arrays of element type R:
+//         (rho, vx, vy, vz, p, Bcx, Bcy, Bcz, Bx_lo, By_lo, Bz_lo), cell indexed;
+//         written by the kernel that produces the state, read with a halo by
+//         the next stage.  Primitive recovery (the paper's first stage,
+//         Sec. 2.2) therefore runs once per cell and state -- in FP64 for the
+//         pressure in the FP64 and mixed forms -- instead of once per halo
+//         copy.
+// One RK2 (Heun) step = stage 1 (W(U^n) -> K1 = L(U^n), W(U*)) and stage 2
+// (W(U*) -> U^{n+1} = U^n + dt/2 (K1 + L(U*)), W(U^{n+1}), CFL max of
+// U^{n+1} for the next step).  U* = U^n + dt K1 is never stored: the ghost
+// faces of outflow boundaries rebuild it from U^n and K1.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,6 +34,8 @@ template <> struct Prec<P_FP32> { using S = float; using R = float; using K = fl
 enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 // counters
 enum { C_RHO_FLOOR = 0, C_P_FLOOR = 1, C_HLL = 2, C_HLLD = 3, C_NCOUNT = 8 };
+// number of primitive arrays
+enum { NW = 11 };
 
 struct Geo {
   int n[3];
@@ -43,6 +45,7 @@ struct Geo {
   double gamma, rho_floor, p_floor, cfl;
   int emf_mean;
   int riemann;     // 0 HLLD, 1 HLL, 2 learned
+  double deadband; // relative deadband on the mass flux orienting the upwind EMF
   int TX, TY, TZ;
   int ntx, nty, nchunk;
   long long ncell;
@@ -50,17 +53,19 @@ struct Geo {
   long long total;         // packed state length (5 ncell + faces)
 };
 
-// Packed state: [rho | mx | my | mz | E | Bx | By | Bz] with the face arrays
-// at face_off[d]; one element type per buffer.
 struct StageArgs {
-  const void* U;     // U^n (type S)
-  const void* K1;    // stage-1 increments (type K), read by stage 2
-  void* OUT;         // stage 1: increments (type K); stage 2: U^{n+1} (type S)
-  unsigned long long* smax;   // CFL max speed sum, bits of a non-negative double
+  const void* U;       // U^n (type S)
+  const void* K1;      // stage-1 increments (type K): written by stage 1, read by stage 2
+  void* K1out;         // stage 1: where L(U^n) goes
+  void* Uout;          // stage 2: U^{n+1}
+  const void* Win;     // primitives of the stage's input state (type R)
+  void* Wout;          // primitives of the stage's output state
+  unsigned long long* dtword;   // CFL max of the step's starting state (bits of a double)
+  unsigned long long* nextword; // stage 2: CFL max of U^{n+1}; stage 1 clears it
   unsigned int* status;
   unsigned long long* counters;
-  double dt;         // > 0: explicit; <= 0: cfl / smax
-  const float* mlp;  // learned-switch weights (packed), or null
+  double dt;           // > 0: explicit; <= 0: cfl / *dtword
+  const float* mlp;    // learned-switch weights (packed), or null
   float mlp_tau;
 };
 
@@ -72,90 +77,100 @@ __host__ __device__ inline int wrapc(int i, int n, int bc) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// Shared-memory layout of the stage kernel, in units of R.
-struct Smem {
-  int TX, TY;
-  int nR, nX, nY, nZ, nE, nC;
-  int oP, oBN, oHX, oHY, oHZ, oXC, oYC, oZC, oEC, oEXY, oEZ, oDU, total;
-  __host__ __device__ void init(int tx, int ty) {
-    TX = tx; TY = ty;
-    nR = (TX + 4) * (TY + 4);
-    nX = (TX + 1) * (TY + 2);
-    nY = (TX + 2) * (TY + 1);
-    nZ = (TX + 2) * (TY + 2);
-    nE = (TX + 1) * (TY + 1);
-    nC = TX * TY;
-    int o = 0;
-    oP = o;   o += 4 * 8 * nR;
-    oBN = o;  o += 2 * 3 * nR;
-    oHX = o;  o += 5 * nX;
-    oHY = o;  o += 5 * nY;
-    oHZ = o;  o += 5 * nZ;
-    oXC = o;  o += 2 * 3 * nX;
-    oYC = o;  o += 2 * 3 * nY;
-    oZC = o;  o += 3 * nZ;
-    oEC = o;  o += 2 * 3 * nZ;
-    oEXY = o; o += 2 * 2 * nE;
-    oEZ = o;  o += nE;
-    oDU = o;  o += 2 * 5 * nC;
-    total = o;
-  }
-};
+// Stored face reference along a normal axis for a (possibly ghost) face
+// index i: value = f(a) + t (f(b) - f(a)).  Periodic axes wrap; outflow axes
+// use the stored faces 0..n and extrapolate linearly beyond them (the ghost
+// normal field that keeps div B = 0 in zero-gradient ghost cells).
+struct FRef { int a, b, t; };
 
-// value of face array d (normal axis d) at cell coordinates c[3] whose normal
-// component may lie outside [0, nf): periodic wraps, outflow extrapolates
-// linearly from the two nearest stored faces.  Returns the two stored indices
-// and the extrapolation weight t: value = f(i0) + t (f(i1) - f(i0)).
-struct FaceRef { long long i0, i1; double t; };
-
-__device__ __forceinline__ FaceRef face_ref(const Geo& g, int d, int ci, int cj, int ck) {
-  int c[3] = {ci, cj, ck};
-  int len[3] = {g.n[0], g.n[1], g.n[2]};
-  len[d] = g.nf[d];
-#pragma unroll
-  for (int e = 0; e < 3; ++e)
-    if (e != d) c[e] = wrapc(c[e], g.n[e], g.bc[e]);
-  int i = c[d];
-  FaceRef r;
-  r.t = 0.0;
-  int a, b;
-  if (g.bc[d] == 0) {
-    a = wrapc(i, g.n[d], 0); b = a;
-  } else if (i >= 0 && i <= g.n[d]) {
-    a = i; b = i;
-  } else if (i < 0) {
-    a = 0; b = 1; r.t = (double)i;
-  } else {
-    a = g.n[d]; b = g.n[d] - 1; r.t = (double)(g.n[d] - i);
-  }
-  c[d] = a;
-  r.i0 = g.face_off[d] + (long long)c[0] + (long long)len[0] * ((long long)c[1] + (long long)len[1] * c[2]);
-  c[d] = b;
-  r.i1 = g.face_off[d] + (long long)c[0] + (long long)len[0] * ((long long)c[1] + (long long)len[1] * c[2]);
+__host__ __device__ inline FRef face_ref1(int i, int n, int bc) {
+  FRef r;
+  if (bc == 0) { r.a = r.b = wrapc(i, n, 0); r.t = 0; }
+  else if (i >= 0 && i <= n) { r.a = r.b = i; r.t = 0; }
+  else if (i < 0) { r.a = 0; r.b = 1; r.t = i; }
+  else { r.a = n; r.b = n - 1; r.t = n - i; }
   return r;
 }
 
-template <int PREC, int STAGE>
-__device__ __forceinline__ double state_at(const StageArgs& a, long long idx, double dt) {
-  using S = typename Prec<PREC>::S;
-  using K = typename Prec<PREC>::K;
-  double u = (double)((const S*)a.U)[idx];
-  if (STAGE == 2) u = u + dt * (double)((const K*)a.K1)[idx];
-  return u;
+// Primitive recovery of one cell from conserved values (rho, m, E) and the
+// two faces of each axis: v = m/rho, B_c = face means, p = (gamma-1)(E -
+// |m|^2/(2 rho) - |B_c|^2/2), floors on rho and p.  FP64 and mixed forms
+// recover p in FP64; the mixed form refines the FP32 reciprocal of rho with
+// one FP64 Newton step (relative error ~1e-14) and returns FP32 primitives.
+template <int PREC>
+__device__ __forceinline__ void recover(const Geo& g, double rho, double mx, double my, double mz, double e,
+                                        double bxl, double bxh, double byl, double byh, double bzl, double bzh,
+                                        typename Prec<PREC>::R* w, int& rho_hit, int& p_hit) {
+  using R = typename Prec<PREC>::R;
+  rho_hit = rho < g.rho_floor;
+  if (rho_hit) rho = g.rho_floor;
+  const double sx = bxl + bxh, sy = byl + byh, sz = bzl + bzh;
+  const double mm = mx * mx + my * my + mz * mz;
+  const double bb = sx * sx + sy * sy + sz * sz;
+  if (PREC == P_FP64) {
+    const double rinv = 1.0 / rho;
+    double p = (g.gamma - 1.0) * (e - 0.5 * mm * rinv - 0.125 * bb);
+    p_hit = p < g.p_floor;
+    if (p_hit) p = g.p_floor;
+    w[0] = (R)rho; w[1] = (R)(mx * rinv); w[2] = (R)(my * rinv); w[3] = (R)(mz * rinv); w[4] = (R)p;
+    w[5] = (R)(0.5 * sx); w[6] = (R)(0.5 * sy); w[7] = (R)(0.5 * sz);
+  } else {
+    const float rf = 1.0f / (float)rho;
+    const double r0 = (double)rf;
+    const double r1 = fma(r0, fma(-rho, r0, 1.0), r0);
+    double p = (g.gamma - 1.0) * (e - 0.5 * mm * r1 - 0.125 * bb);
+    p_hit = p < g.p_floor;
+    if (p_hit) p = g.p_floor;
+    w[0] = (R)rho; w[1] = (R)mx * rf; w[2] = (R)my * rf; w[3] = (R)mz * rf; w[4] = (R)p;
+    w[5] = 0.5f * (R)sx; w[6] = 0.5f * (R)sy; w[7] = 0.5f * (R)sz;
+  }
+  w[8] = (R)bxl; w[9] = (R)byl; w[10] = (R)bzl;
 }
 
-template <int PREC, int STAGE>
-__device__ __forceinline__ float state_at_f(const StageArgs& a, long long idx, float dt) {
-  using S = typename Prec<PREC>::S;
-  using K = typename Prec<PREC>::K;
-  float u = (float)((const S*)a.U)[idx];
-  if (STAGE == 2) u = u + dt * (float)((const K*)a.K1)[idx];
-  return u;
+// FP32 state form: everything in FP32.
+template <>
+__device__ __forceinline__ void recover<P_FP32>(const Geo& g, double rho, double mx, double my, double mz, double e,
+                                                double bxl, double bxh, double byl, double byh, double bzl,
+                                                double bzh, float* w, int& rho_hit, int& p_hit) {
+  float r = (float)rho;
+  rho_hit = r < (float)g.rho_floor;
+  if (rho_hit) r = (float)g.rho_floor;
+  const float rinv = 1.0f / r;
+  const float fx = (float)mx, fy = (float)my, fz = (float)mz;
+  const float bx = 0.5f * ((float)bxl + (float)bxh), by = 0.5f * ((float)byl + (float)byh),
+              bz = 0.5f * ((float)bzl + (float)bzh);
+  float p = (float)(g.gamma - 1.0) * ((float)e - 0.5f * (fx * fx + fy * fy + fz * fz) * rinv -
+                                      0.5f * (bx * bx + by * by + bz * bz));
+  p_hit = p < (float)g.p_floor;
+  if (p_hit) p = (float)g.p_floor;
+  w[0] = r; w[1] = fx * rinv; w[2] = fy * rinv; w[3] = fz * rinv; w[4] = p;
+  w[5] = bx; w[6] = by; w[7] = bz;
+  w[8] = (float)bxl; w[9] = (float)byl; w[10] = (float)bzl;
 }
 
-// launchers defined next to the kernel (stage_kernel.cu)
-cudaError_t launch_stage(int prec, int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
-                         const StageArgs& a);
-cudaError_t stage_set_smem(int prec, size_t bytes);
+// CFL speed sum of one cell from its primitives: sum over the active axes of
+// (|v_d| + c_f,d) / Delta_d, c_f,d taken with the cell-centred B_d as normal.
+template <typename R>
+__device__ __forceinline__ R cfl_speed(const Geo& g, const R* w) {
+  R sum = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (g.n[d] > 1) {
+      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      R q[7] = {w[0], w[1 + d], w[1 + t1], w[1 + t2], w[4], w[5 + t1], w[5 + t2]};
+      const R cf = fast_speed(q, w[5 + d], (R)g.gamma);
+      sum += (rabs(q[1]) + cf) * (R)g.inv_d[d];
+    }
+  }
+  return sum;
+}
+
+// launchers defined next to the kernels (one translation unit per precision)
+cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nblocks, size_t smem, cudaStream_t st,
+                         const Geo& g, const StageArgs& a);
+cudaError_t launch_prims(int prec, unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& a);
+cudaError_t stage_set_smem(int prec, int tx, int ty, size_t bytes);
+size_t stage_smem_bytes(int prec, int tx, int ty);
+bool stage_tile_supported(int prec, int tx, int ty);
 
 }  // namespace mhd

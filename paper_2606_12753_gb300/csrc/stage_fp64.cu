@@ -1,0 +1,51 @@
+// Stage-kernel instantiations and launchers for the fp64 form.
+#include "stage_impl.cuh"
+
+namespace mhd {
+
+#define MHD_TILES(X) X(16, 8) X(24, 8) X(8, 8)
+
+cudaError_t launch_stage_fp64(int stage, int tx, int ty, unsigned nblocks, size_t smem, cudaStream_t st,
+                                 const Geo& g, const StageArgs& args) {
+#define X(TXv, TYv)                                                                              \
+  if (tx == TXv && ty == TYv) {                                                                  \
+    if (stage == 1) stage_kernel<P_FP64, 1, TXv, TYv><<<nblocks, 256, smem, st>>>(g, args);     \
+    else stage_kernel<P_FP64, 2, TXv, TYv><<<nblocks, 256, smem, st>>>(g, args);                \
+    return cudaGetLastError();                                                                   \
+  }
+  MHD_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t set_smem_fp64(int tx, int ty, size_t bytes) {
+#define X(TXv, TYv)                                                                                        \
+  if (tx == TXv && ty == TYv) {                                                                            \
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<P_FP64, 1, TXv, TYv>,                              \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);         \
+    if (e == cudaSuccess)                                                                                  \
+      e = cudaFuncSetAttribute(stage_kernel<P_FP64, 2, TXv, TYv>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               (int)bytes);                                                                \
+    return e;                                                                                              \
+  }
+  MHD_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+size_t smem_bytes_fp64(int tx, int ty) {
+  using R = Prec<P_FP64>::R;
+  using S = Prec<P_FP64>::S;
+#define X(TXv, TYv) \
+  if (tx == TXv && ty == TYv) return Tile<TXv, TYv>::bytes<R, S>();
+  MHD_TILES(X)
+#undef X
+  return 0;
+}
+
+cudaError_t launch_prims_fp64(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
+  prims_kernel<P_FP64><<<nblocks, 256, 0, st>>>(g, args);
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -1,0 +1,538 @@
+// Fused z-marching RK2 stage kernel, templated on precision, stage and tile.
+//
+// One CTA owns a TX x TY column of cells and marches along z through a chunk
+// of TZ planes.  Per output plane k:
+//   A  load plane k+2 of the input state's primitives (tile + 2-cell halo)
+//      into a 4-plane shared-memory ring; periodic axes wrap by index, outflow
+//      ghost cells copy the nearest interior cell's primitives with the
+//      normal field on their faces extrapolated linearly (div B = 0);
+//   B  PLM-MC reconstruction + Riemann solve (HLLD / HLL) on the z-faces k+1/2
+//      and on the x- and y-faces of plane k+1 (one halo row across, for the
+//      edge EMFs), and the cell-centred EMF -v x B of plane k+1;
+//   C  flux divergence and the Gardiner-Stone edge EMFs E_z(k), E_x, E_y(k+1/2);
+//   D  new face values (-curl E), then per owned cell the new conserved state,
+//      its primitives (FP64 pressure recovery in the FP64/mixed forms) and,
+//      in stage 2, the CFL speed of U^{n+1}.
+// This is the chain Reconstruct -> HLLD_Solver -> RightHandSide -> CT_EMF ->
+// US of the paper's MHD step (Sec. 2.2, Table 2) fused into one pass per
+// RK stage.
+#pragma once
+#include "stage.cuh"
+
+namespace mhd {
+
+template <int TX, int TY>
+struct Tile {
+  static constexpr int W = TX + 4, H = TY + 4;
+  static constexpr int nR = W * H;
+  static constexpr int nX = (TX + 1) * (TY + 2);
+  static constexpr int nY = (TX + 2) * (TY + 1);
+  static constexpr int nZ = (TX + 2) * (TY + 2);
+  static constexpr int nE = (TX + 1) * (TY + 1);
+  static constexpr int nC = TX * TY;
+  // offsets in units of R
+  static constexpr int oP = 0;
+  static constexpr int oBN = oP + 4 * 8 * nR;
+  static constexpr int oHX = oBN + 2 * 3 * nR;
+  static constexpr int oHY = oHX + 5 * nX;
+  static constexpr int oHZ = oHY + 5 * nY;
+  static constexpr int oXC = oHZ + 5 * nZ;
+  static constexpr int oYC = oXC + 2 * 3 * nX;
+  static constexpr int oZC = oYC + 2 * 3 * nY;
+  static constexpr int oEC = oZC + 3 * nZ;
+  static constexpr int oEXY = oEC + 2 * 3 * nZ;
+  static constexpr int oEZ = oEXY + 2 * 2 * nE;
+  static constexpr int oDU = oEZ + nE;
+  static constexpr int nRtot = oDU + 2 * 5 * nC;
+  // new face values (type S): NBX[nE], NBY[nE], NBZ[2][nC]
+  static constexpr int nS = 2 * nE + 2 * nC;
+  // index tables (int): colc[W], rowc[H]
+  static constexpr int nI = W + H;
+  template <typename R, typename S>
+  static constexpr size_t bytes() {
+    size_t b = (size_t)nRtot * sizeof(R);
+    b = (b + 15) / 16 * 16;
+    b += (size_t)nS * sizeof(S);
+    b = (b + 15) / 16 * 16;
+    b += (size_t)nI * sizeof(int);
+    return b;
+  }
+};
+
+template <int D, typename R>
+__device__ __forceinline__ void gather(const R* ring, int nR, int r, R* w) {
+  // (rho, vx, vy, vz, p, Bcx, Bcy, Bcz) -> (rho, v_n, v_t1, v_t2, p, B_t1, B_t2)
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  w[0] = ring[0 * nR + r];
+  w[1] = ring[(1 + D) * nR + r];
+  w[2] = ring[(1 + t1) * nR + r];
+  w[3] = ring[(1 + t2) * nR + r];
+  w[4] = ring[4 * nR + r];
+  w[5] = ring[(5 + t1) * nR + r];
+  w[6] = ring[(5 + t2) * nR + r];
+}
+
+// conserved value of the stage's input state: U^n (stage 1) or
+// U* = U^n + dt K1 (stage 2), in the arithmetic of the stage's own update
+template <int PREC, int STAGE>
+__device__ __forceinline__ double cons_at(const StageArgs& a, long long idx, double dt) {
+  using S = typename Prec<PREC>::S;
+  using K = typename Prec<PREC>::K;
+  if (PREC == P_FP32) {
+    float u = (float)((const S*)a.U)[idx];
+    if (STAGE == 2) u = u + (float)dt * (float)((const K*)a.K1)[idx];
+    return (double)u;
+  }
+  double u = (double)((const S*)a.U)[idx];
+  if (STAGE == 2) u = fma(dt, (double)((const K*)a.K1)[idx], u);
+  return u;
+}
+
+// Value of face array d at a (possibly ghost) normal index, transverse
+// coordinates already mapped into the box, in the stage's input state.
+template <int PREC, int STAGE>
+__device__ __forceinline__ double face_value(const Geo& g, const StageArgs& a, double dt, int d, int c0, int c1,
+                                             int c2, int raw) {
+  int c[3] = {c0, c1, c2};
+  const FRef fr = face_ref1(raw, g.n[d], g.bc[d]);
+  int len[3] = {g.n[0], g.n[1], g.n[2]};
+  len[d] = g.nf[d];
+  c[d] = fr.a;
+  const long long ia = g.face_off[d] + c[0] + (long long)len[0] * (c[1] + (long long)len[1] * c[2]);
+  const double f0 = cons_at<PREC, STAGE>(a, ia, dt);
+  if (!fr.t) return f0;
+  c[d] = fr.b;
+  const long long ib = g.face_off[d] + c[0] + (long long)len[0] * (c[1] + (long long)len[1] * c[2]);
+  const double f1 = cons_at<PREC, STAGE>(a, ib, dt);
+  return f0 + (double)fr.t * (f1 - f0);
+}
+
+// Primitives of an interior cell from the conserved state of the stage's
+// input (U^n in stage 1, U^n + dt K1 in stage 2) and its own faces.
+template <int PREC, int STAGE>
+__device__ void cell_prims(const Geo& g, const StageArgs& a, double dt, int i, int j, int k,
+                           typename Prec<PREC>::R* w, int& rho_hit, int& p_hit) {
+  const long long s = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+  double u[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = cons_at<PREC, STAGE>(a, v * g.ncell + s, dt);
+  const double bxl = face_value<PREC, STAGE>(g, a, dt, 0, i, j, k, i);
+  const double bxh = face_value<PREC, STAGE>(g, a, dt, 0, i, j, k, i + 1);
+  const double byl = face_value<PREC, STAGE>(g, a, dt, 1, i, j, k, j);
+  const double byh = face_value<PREC, STAGE>(g, a, dt, 1, i, j, k, j + 1);
+  const double bzl = face_value<PREC, STAGE>(g, a, dt, 2, i, j, k, k);
+  const double bzh = face_value<PREC, STAGE>(g, a, dt, 2, i, j, k, k + 1);
+  recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], bxl, bxh, byl, byh, bzl, bzh, w, rho_hit, p_hit);
+}
+
+template <int PREC, int STAGE, int TX, int TY>
+struct StageKernel {
+  using R = typename Prec<PREC>::R;
+  using S = typename Prec<PREC>::S;
+  using K = typename Prec<PREC>::K;
+  using T = Tile<TX, TY>;
+  static constexpr int W = T::W;
+
+  // ---------------------------------------------------------------- phase A
+  static __device__ __forceinline__ void load_plane(const Geo& g, const StageArgs& a, R* sm, const int* colc,
+                                                    const int* rowc, double dt, int gi0, int gj0, int m,
+                                                    bool write_bn) {
+    R* P = sm + T::oP + (m & 3) * 8 * T::nR;
+    R* BN = sm + T::oBN + (m & 1) * 3 * T::nR;
+    const bool zin = g.bc[2] == 0 || (m >= 0 && m < g.n[2]);
+    const int ck = wrapc(m, g.n[2], g.bc[2]);
+    const R* Win = (const R*)a.Win;
+    for (int r = threadIdx.x; r < T::nR; r += blockDim.x) {
+      const int x = r % W, y = r / W;
+      const int gi = gi0 - 2 + x, gj = gj0 - 2 + y;
+      const bool inside = zin && (g.bc[0] == 0 || (gi >= 0 && gi < g.n[0])) &&
+                          (g.bc[1] == 0 || (gj >= 0 && gj < g.n[1]));
+      R w[NW];
+      const long long s = (long long)colc[x] + (long long)g.n[0] * ((long long)rowc[y] + (long long)g.n[1] * ck);
+#pragma unroll
+      for (int v = 0; v < NW; ++v) w[v] = Win[v * g.ncell + s];
+      if (!inside) {
+        // outflow ghost: rho, v, p of the nearest interior cell; along each
+        // axis on which the cell is a ghost, the normal field on its faces is
+        // the linear extrapolation and B_c is their mean
+        const int raw[3] = {gi, gj, m};
+        const int cc[3] = {colc[x], rowc[y], ck};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (g.bc[d] == 1 && (raw[d] < 0 || raw[d] >= g.n[d])) {
+            const double lo = face_value<PREC, STAGE>(g, a, dt, d, cc[0], cc[1], cc[2], raw[d]);
+            const double hi = face_value<PREC, STAGE>(g, a, dt, d, cc[0], cc[1], cc[2], raw[d] + 1);
+            w[5 + d] = (R)(0.5 * (lo + hi));
+            w[8 + d] = (R)lo;
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 8; ++v) P[v * T::nR + r] = w[v];
+      if (write_bn) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) BN[d * T::nR + r] = w[8 + d];
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- phase B
+  template <int D>
+  static __device__ __forceinline__ void face(const Geo& g, R* sm, const R (&c)[4][7], R bn, R* H, R* C, int n,
+                                              int out) {
+    R wl[7], wr[7], f[7], cm;
+    plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+    const R gam = (R)g.gamma;
+    if (g.riemann == 1) hll_flux(wl, wr, bn, gam, f, &cm);
+    else hlld_flux(wl, wr, bn, gam, f, &cm);
+    // hydro flux back in (rho, mx, my, mz, E) order
+    H[0 * n + out] = f[0];
+    H[(1 + D) * n + out] = f[1];
+    H[(1 + (D + 1) % 3) * n + out] = f[2];
+    H[(1 + (D + 2) % 3) * n + out] = f[3];
+    H[4 * n + out] = f[4];
+    // CT parts: EMF of the t2 edge (-F(B_t1)), of the t1 edge (+F(B_t2)), orienting mass flux
+    C[out] = -f[5];
+    C[n + out] = f[6];
+    C[2 * n + out] = oriented_mass_flux(f[0], wl[0], wr[0], cm, (R)g.deadband);
+  }
+
+  static __device__ __forceinline__ void fluxes(const Geo& g, R* sm, int k, int q, bool with_z) {
+    const int nZ = with_z ? T::nZ : 0;
+    const int nitems = nZ + T::nX + T::nY;
+    const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
+    const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
+    for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
+      R c[4][7];
+      if (w < nZ) {
+        const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
+        const int r = (i + 2) + W * (j + 2);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) gather<2>(sm + T::oP + ((k - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
+        const R bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
+        face<2>(g, sm, c, bn, sm + T::oHZ, sm + T::oZC, T::nZ, w);
+      } else if (w < nZ + T::nX) {
+        const int o = w - nZ;
+        const int i = o % (TX + 1), j = o / (TX + 1) - 1;
+        const int r = (i + 2) + W * (j + 2);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) gather<0>(Pq, T::nR, r - 2 + s, c[s]);
+        face<0>(g, sm, c, BNq[r], sm + T::oHX, sm + T::oXC + (q & 1) * 3 * T::nX, T::nX, o);
+      } else {
+        const int o = w - nZ - T::nX;
+        const int i = o % (TX + 2) - 1, j = o / (TX + 2);
+        const int r = (i + 2) + W * (j + 2);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) gather<1>(Pq, T::nR, r + (s - 2) * W, c[s]);
+        face<1>(g, sm, c, BNq[T::nR + r], sm + T::oHY, sm + T::oYC + (q & 1) * 3 * T::nY, T::nY, o);
+      }
+    }
+    // cell-centred E_c = -v x B_c of plane q
+    R* EC = sm + T::oEC + (q & 1) * 3 * T::nZ;
+    for (int w = threadIdx.x; w < T::nZ; w += blockDim.x) {
+      const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
+      const int r = (i + 2) + W * (j + 2);
+      const R vx = Pq[1 * T::nR + r], vy = Pq[2 * T::nR + r], vz = Pq[3 * T::nR + r];
+      const R bx = Pq[5 * T::nR + r], by = Pq[6 * T::nR + r], bz = Pq[7 * T::nR + r];
+      EC[w] = vz * by - vy * bz;
+      EC[T::nZ + w] = vx * bz - vz * bx;
+      EC[2 * T::nZ + w] = vy * bx - vx * by;
+    }
+  }
+
+  // ---------------------------------------------------------------- phase C
+  static __device__ __forceinline__ void divergence_and_edges(const Geo& g, R* sm, int k) {
+    const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1], idz = (R)g.inv_d[2];
+    const int sk = k & 1, sk1 = (k + 1) & 1;
+    R* DUk = sm + T::oDU + sk * 5 * T::nC;
+    R* DUk1 = sm + T::oDU + sk1 * 5 * T::nC;
+    const R* HX = sm + T::oHX;
+    const R* HY = sm + T::oHY;
+    const R* HZ = sm + T::oHZ;
+    for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
+      const int i = c % TX, j = c / TX;
+      const int iz = (i + 1) + (TX + 2) * (j + 1);
+      const int ixm = i + (TX + 1) * (j + 1), ixp = ixm + 1;
+      const int iym = (i + 1) + (TX + 2) * j, iyp = iym + (TX + 2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R hz = HZ[v * T::nZ + iz];
+        DUk[v * T::nC + c] -= hz * idz;
+        DUk1[v * T::nC + c] = hz * idz - (HX[v * T::nX + ixp] - HX[v * T::nX + ixm]) * idx -
+                              (HY[v * T::nY + iyp] - HY[v * T::nY + iym]) * idy;
+      }
+    }
+    const bool mean = g.emf_mean != 0;
+    const R* XCk = sm + T::oXC + sk * 3 * T::nX;
+    const R* XCk1 = sm + T::oXC + sk1 * 3 * T::nX;
+    const R* YCk = sm + T::oYC + sk * 3 * T::nY;
+    const R* YCk1 = sm + T::oYC + sk1 * 3 * T::nY;
+    const R* ZC = sm + T::oZC;
+    const R* ECk = sm + T::oEC + sk * 3 * T::nZ;
+    const R* ECk1 = sm + T::oEC + sk1 * 3 * T::nZ;
+    R* EZ = sm + T::oEZ;
+    R* EX1 = sm + T::oEXY + sk1 * 2 * T::nE;   // edges at k+1/2
+    R* EY1 = EX1 + T::nE;
+    constexpr int nX = T::nX, nY = T::nY, nZ = T::nZ;
+    for (int e = threadIdx.x; e < T::nE; e += blockDim.x) {
+      const int i = e % (TX + 1), j = e / (TX + 1);
+      {  // E_z at (i-1/2, j-1/2), plane k
+        const int xa = i + (TX + 1) * j, xb = xa + (TX + 1);
+        const int ya = i + (TX + 2) * j, yb = ya + 1;
+        const int c_mm = i + (TX + 2) * j, c_pm = c_mm + 1, c_mp = c_mm + (TX + 2), c_pp = c_mp + 1;
+        EZ[e] = edge_emf<R>(XCk[xa], XCk[xb], XCk[2 * nX + xa], XCk[2 * nX + xb], YCk[nY + ya], YCk[nY + yb],
+                            YCk[2 * nY + ya], YCk[2 * nY + yb], ECk[2 * nZ + c_mm], ECk[2 * nZ + c_pm],
+                            ECk[2 * nZ + c_mp], ECk[2 * nZ + c_pp], mean);
+      }
+      if (i < TX) {  // E_x at (i, j-1/2, k+1/2)
+        const int ya = (i + 1) + (TX + 2) * j;
+        const int za = (i + 1) + (TX + 2) * j, zb = za + (TX + 2);
+        EX1[e] = edge_emf<R>(YCk[ya], YCk1[ya], YCk[2 * nY + ya], YCk1[2 * nY + ya], ZC[nZ + za], ZC[nZ + zb],
+                             ZC[2 * nZ + za], ZC[2 * nZ + zb], ECk[za], ECk[zb], ECk1[za], ECk1[zb], mean);
+      }
+      if (j < TY) {  // E_y at (i-1/2, j, k+1/2)
+        const int za = i + (TX + 2) * (j + 1), zb = za + 1;
+        const int xa = i + (TX + 1) * (j + 1);
+        EY1[e] = edge_emf<R>(ZC[za], ZC[zb], ZC[2 * nZ + za], ZC[2 * nZ + zb], XCk[nX + xa], XCk1[nX + xa],
+                             XCk[2 * nX + xa], XCk1[2 * nX + xa], ECk[nZ + za], ECk1[nZ + za], ECk[nZ + zb],
+                             ECk1[nZ + zb], mean);
+      }
+    }
+  }
+
+  // new value of one conserved quantity from its increment l:
+  // stage 1 U* = U^n + dt K1 (K1 = l rounded to K), stage 2 U^n + dt/2 (K1 + l)
+  static __device__ __forceinline__ S advance(const StageArgs& a, long long gidx, R l, double dt) {
+    const S un = ((const S*)a.U)[gidx];
+    if (STAGE == 1) {
+      const K k1 = (K)l;
+      if (PREC == P_FP32) return un + (float)dt * k1;
+      return (S)fma(dt, (double)k1, (double)un);
+    } else {
+      const K k1 = ((const K*)a.K1)[gidx];
+      if (PREC == P_FP32) return un + (float)(0.5 * dt) * (k1 + (float)l);
+      if (PREC == P_MIXED) return fma(0.5 * dt, (double)(k1 + (float)l), (double)un);
+      return (S)((double)un + 0.5 * dt * ((double)k1 + (double)l));
+    }
+  }
+
+  static __device__ __forceinline__ void emit(const StageArgs& a, long long gidx, R l, S v) {
+    if (STAGE == 1) ((K*)a.K1out)[gidx] = (K)l;
+    else ((S*)a.Uout)[gidx] = v;
+  }
+
+  static __device__ __forceinline__ long long xface_index(const Geo& g, int gi, int gj, int k) {
+    return g.face_off[0] + (long long)gi + (long long)g.nf[0] * ((long long)gj + (long long)g.n[1] * k);
+  }
+  static __device__ __forceinline__ long long yface_index(const Geo& g, int gi, int gj, int k) {
+    return g.face_off[1] + (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.nf[1] * k);
+  }
+  static __device__ __forceinline__ long long zface_index(const Geo& g, int gi, int gj, int k) {
+    return g.face_off[2] + (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k);
+  }
+
+  // ---------------------------------------------------------------- phase D
+  static __device__ __forceinline__ void new_faces(const Geo& g, const StageArgs& a, R* sm, S* NB, double dt,
+                                                   int gi0, int gj0, int k) {
+    const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1], idz = (R)g.inv_d[2];
+    const R* EZ = sm + T::oEZ;
+    const R* EX0 = sm + T::oEXY + (k & 1) * 2 * T::nE;   // k-1/2
+    const R* EY0 = EX0 + T::nE;
+    const R* EX1 = sm + T::oEXY + ((k + 1) & 1) * 2 * T::nE;   // k+1/2
+    const R* EY1 = EX1 + T::nE;
+    S* NBX = NB;
+    S* NBY = NB + T::nE;
+    S* NBZ = NB + 2 * T::nE;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const bool outx = g.bc[0] == 1, outy = g.bc[1] == 1, outz = g.bc[2] == 1;
+    for (int e = threadIdx.x; e < T::nE; e += blockDim.x) {
+      const int i = e % (TX + 1), j = e / (TX + 1);
+      const int gi = gi0 + i, gj = gj0 + j;
+      // B_x on face (i-1/2, j, k): needed for i in [0, TX] within the domain
+      if (j < TY && gj < ny && gi <= nx) {
+        const int fi = gi == nx && !outx ? 0 : gi;
+        const long long f = xface_index(g, fi, gj, k);
+        const R l = -((EZ[e + (TX + 1)] - EZ[e]) * idy - (EY1[e] - EY0[e]) * idz);
+        const S v = advance(a, f, l, dt);
+        NBX[e] = v;
+        if ((i < TX && gi < nx) || (outx && gi == nx)) emit(a, f, l, v);
+      }
+      // B_y on face (i, j-1/2, k)
+      if (i < TX && gi < nx && gj <= ny) {
+        const int fj = gj == ny && !outy ? 0 : gj;
+        const long long f = yface_index(g, gi, fj, k);
+        const R l = -((EX1[e] - EX0[e]) * idz - (EZ[e + 1] - EZ[e]) * idx);
+        const S v = advance(a, f, l, dt);
+        NBY[e] = v;
+        if ((j < TY && gj < ny) || (outy && gj == ny)) emit(a, f, l, v);
+      }
+      // B_z on the faces k-1/2 (owned) and k+1/2 of cell (i, j)
+      if (i < TX && j < TY && gi < nx && gj < ny) {
+        const int c = i + TX * j;
+        const long long flo = zface_index(g, gi, gj, k);
+        const R llo = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
+        const S vlo = advance(a, flo, llo, dt);
+        NBZ[c] = vlo;
+        emit(a, flo, llo, vlo);
+        const int khi = k + 1 == nz && !outz ? 0 : k + 1;
+        const long long fhi = zface_index(g, gi, gj, khi);
+        const R lhi = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
+        const S vhi = advance(a, fhi, lhi, dt);
+        NBZ[T::nC + c] = vhi;
+        if (outz && k + 1 == nz) emit(a, fhi, lhi, vhi);
+      }
+    }
+  }
+
+  static __device__ __forceinline__ void new_cells(const Geo& g, const StageArgs& a, R* sm, const S* NB, double dt,
+                                                   int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
+                                                   bool& bad, R& smax) {
+    const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
+    const S* NBX = NB;
+    const S* NBY = NB + T::nE;
+    const S* NBZ = NB + 2 * T::nE;
+    R* Wout = (R*)a.Wout;
+    const int nx = g.n[0], ny = g.n[1];
+    for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
+      const int i = c % TX, j = c / TX;
+      const int gi = gi0 + i, gj = gj0 + j;
+      if (gi >= nx || gj >= ny) continue;
+      const long long s = (long long)gi + (long long)nx * ((long long)gj + (long long)ny * k);
+      double u[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R l = DU[v * T::nC + c];
+        const S nv = advance(a, v * g.ncell + s, l, dt);
+        emit(a, v * g.ncell + s, l, nv);
+        u[v] = (double)nv;
+      }
+      if (!a.Wout) continue;   // operator evaluation only (mhd_rhs)
+      const int e = i + (TX + 1) * j;
+      R w[NW];
+      int hr, hp;
+      recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], (double)NBX[e], (double)NBX[e + 1], (double)NBY[e],
+                    (double)NBY[e + (TX + 1)], (double)NBZ[c], (double)NBZ[T::nC + c], w, hr, hp);
+      nrho += hr;
+      np += hp;
+      if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
+#pragma unroll
+      for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
+      if (STAGE == 2) {
+        const R sp = cfl_speed<R>(g, w);
+        smax = sp > smax ? sp : smax;
+      }
+    }
+  }
+
+  // One work item: tile `item` (x fastest, then y, then z chunk) of one box.
+  // Shared memory is the caller's dynamic allocation; every thread of the
+  // CTA calls this with the same arguments.
+  static __device__ void run_item(const Geo& g, const StageArgs& a, int item, unsigned char* smem_raw) {
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    constexpr size_t sOff = ((size_t)T::nRtot * sizeof(R) + 15) / 16 * 16;
+    S* NB = reinterpret_cast<S*>(smem_raw + sOff);
+    constexpr size_t iOff = ((sOff + (size_t)T::nS * sizeof(S)) + 15) / 16 * 16;
+    int* colc = reinterpret_cast<int*>(smem_raw + iOff);
+    int* rowc = colc + W;
+
+    int b = item;
+    const int tile_x = b % g.ntx;
+    b /= g.ntx;
+    const int tile_y = b % g.nty;
+    const int chunk = b / g.nty;
+    const int gi0 = tile_x * TX, gj0 = tile_y * TY;
+    const int kb = chunk * g.TZ;
+    const int ke = min(kb + g.TZ, g.n[2]);
+
+    if (STAGE == 1 && item == 0 && threadIdx.x == 0) *a.nextword = 0ull;
+    double dt = a.dt;
+    if (!(dt > 0.0)) {
+      const double m = __longlong_as_double((long long)*a.dtword);
+      dt = m > 0.0 ? g.cfl / m : 0.0;
+    }
+    __syncthreads();   // the previous item of this CTA may still read the tables
+    for (int t = threadIdx.x; t < T::W + T::H; t += blockDim.x) {
+      if (t < T::W) colc[t] = wrapc(gi0 - 2 + t, g.n[0], g.bc[0]);
+      else rowc[t - T::W] = wrapc(gj0 - 2 + (t - T::W), g.n[1], g.bc[1]);
+    }
+    __syncthreads();
+
+    unsigned nrho = 0, np = 0;
+    bool bad = false;
+    R smax = R(0);
+
+    load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 2, false);
+    load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 1, true);
+    load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb, true);
+    __syncthreads();
+    fluxes(g, sm, kb - 2, kb - 1, false);
+    __syncthreads();
+    for (int k = kb - 1; k < ke; ++k) {
+      load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true);
+      __syncthreads();
+      fluxes(g, sm, k, k + 1, true);
+      __syncthreads();
+      divergence_and_edges(g, sm, k);
+      __syncthreads();
+      if (k >= kb) {
+        new_faces(g, a, sm, NB, dt, gi0, gj0, k);
+        __syncthreads();
+        new_cells(g, a, sm, NB, dt, gi0, gj0, k, nrho, np, bad, smax);
+      }
+    }
+
+    const unsigned mask = 0xffffffffu;
+    nrho = __reduce_add_sync(mask, nrho);
+    np = __reduce_add_sync(mask, np);
+    const unsigned anybad = __any_sync(mask, bad);
+    double sm64 = (double)smax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sm64 = fmax(sm64, __shfl_xor_sync(mask, sm64, o));
+    if ((threadIdx.x & 31) == 0) {
+      if (nrho) atomicAdd(&a.counters[C_RHO_FLOOR], (unsigned long long)nrho);
+      if (np) atomicAdd(&a.counters[C_P_FLOOR], (unsigned long long)np);
+      if (anybad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+      if (STAGE == 2 && sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
+    }
+  }
+};
+
+template <int PREC, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(256) stage_kernel(Geo g, StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageKernel<PREC, STAGE, TX, TY>::run_item(g, a, blockIdx.x, smem_raw);
+}
+
+// Primitives (and the CFL max) of a state set from outside: one thread per cell.
+template <int PREC>
+__global__ void __launch_bounds__(256) prims_kernel(Geo g, StageArgs a) {
+  using R = typename Prec<PREC>::R;
+  R smax = R(0);
+  bool bad = false;
+  R* Wout = (R*)a.Wout;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.ncell;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(s % g.n[0]);
+    const int j = (int)((s / g.n[0]) % g.n[1]);
+    const int k = (int)(s / ((long long)g.n[0] * g.n[1]));
+    R w[NW];
+    int hr, hp;
+    cell_prims<PREC, 1>(g, a, 0.0, i, j, k, w, hr, hp);
+    if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
+#pragma unroll
+    for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
+    const R sp = cfl_speed<R>(g, w);
+    smax = sp > smax ? sp : smax;
+  }
+  const unsigned mask = 0xffffffffu;
+  const unsigned anybad = __any_sync(mask, bad);
+  double sm64 = (double)smax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sm64 = fmax(sm64, __shfl_xor_sync(mask, sm64, o));
+  if ((threadIdx.x & 31) == 0) {
+    if (anybad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    if (sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
+  }
+}
+
+}  // namespace mhd

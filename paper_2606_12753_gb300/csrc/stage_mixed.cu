@@ -1,0 +1,51 @@
+// Stage-kernel instantiations and launchers for the mixed form.
+#include "stage_impl.cuh"
+
+namespace mhd {
+
+#define MHD_TILES(X) X(16, 8) X(16, 16) X(32, 8) X(24, 8) X(8, 8)
+
+cudaError_t launch_stage_mixed(int stage, int tx, int ty, unsigned nblocks, size_t smem, cudaStream_t st,
+                                 const Geo& g, const StageArgs& args) {
+#define X(TXv, TYv)                                                                              \
+  if (tx == TXv && ty == TYv) {                                                                  \
+    if (stage == 1) stage_kernel<P_MIXED, 1, TXv, TYv><<<nblocks, 256, smem, st>>>(g, args);     \
+    else stage_kernel<P_MIXED, 2, TXv, TYv><<<nblocks, 256, smem, st>>>(g, args);                \
+    return cudaGetLastError();                                                                   \
+  }
+  MHD_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t set_smem_mixed(int tx, int ty, size_t bytes) {
+#define X(TXv, TYv)                                                                                        \
+  if (tx == TXv && ty == TYv) {                                                                            \
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<P_MIXED, 1, TXv, TYv>,                              \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);         \
+    if (e == cudaSuccess)                                                                                  \
+      e = cudaFuncSetAttribute(stage_kernel<P_MIXED, 2, TXv, TYv>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               (int)bytes);                                                                \
+    return e;                                                                                              \
+  }
+  MHD_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+size_t smem_bytes_mixed(int tx, int ty) {
+  using R = Prec<P_MIXED>::R;
+  using S = Prec<P_MIXED>::S;
+#define X(TXv, TYv) \
+  if (tx == TXv && ty == TYv) return Tile<TXv, TYv>::bytes<R, S>();
+  MHD_TILES(X)
+#undef X
+  return 0;
+}
+
+cudaError_t launch_prims_mixed(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
+  prims_kernel<P_MIXED><<<nblocks, 256, 0, st>>>(g, args);
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

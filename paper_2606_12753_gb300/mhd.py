@@ -52,7 +52,7 @@ class MHDError(RuntimeError):
 _VP = C.c_void_p
 _H = C.c_void_p
 EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state", "mhd_step",
-           "mhd_step_async", "mhd_set_profiling", "mhd_get_profile", "mhd_cfl_dt", "mhd_divb_max",
+           "mhd_step_async", "mhd_rhs", "mhd_set_profiling", "mhd_get_profile", "mhd_cfl_dt", "mhd_divb_max",
            "mhd_get_stats", "mhd_destroy", "mhd_last_error"]
 
 _lib = None
@@ -84,6 +84,8 @@ def load(build: bool = True):
     L.mhd_step.argtypes = [_H, C.c_double, C.c_int]
     L.mhd_step_async.restype = C.c_int
     L.mhd_step_async.argtypes = [_H, C.c_double, C.c_int]
+    L.mhd_rhs.restype = C.c_int
+    L.mhd_rhs.argtypes = [_H, _VP * 5, _VP * 3, C.c_int]
     L.mhd_set_profiling.restype = C.c_int
     L.mhd_set_profiling.argtypes = [_H, C.c_int]
     L.mhd_get_profile.restype = C.c_int
@@ -137,6 +139,10 @@ def mhd_step(h, dt: float, nsteps: int = 1):
 
 def mhd_step_async(h, dt: float, nsteps: int = 1):
     _check(h, load().mhd_step_async(h, dt, nsteps))
+
+
+def mhd_rhs(h, cell_ptrs, face_ptrs, on_device: int):
+    _check(h, load().mhd_rhs(h, (_VP * 5)(*cell_ptrs), (_VP * 3)(*face_ptrs), on_device))
 
 
 def mhd_set_profiling(h, on: bool):
@@ -229,6 +235,15 @@ class Solver:
         cell = np.empty((5,) + self.dims[::-1], dtype=self.dtype)
         face = [np.empty(s, dtype=self.dtype) for s in self.face_shapes()]
         mhd_get_state(self.h, [cell[v].ctypes.data for v in range(5)], [f.ctypes.data for f in face], 0)
+        return cell, face
+
+    def rhs(self):
+        """L(U) of the current state as (dU/dt cells, [dBx/dt, dBy/dt, dBz/dt])
+        in the increment type (float64 for fp64, float32 otherwise)."""
+        kt = np.float64 if self.cfg.precision == MHD_FP64 else np.float32
+        cell = np.empty((5,) + self.dims[::-1], dtype=kt)
+        face = [np.empty(s, dtype=kt) for s in self.face_shapes()]
+        mhd_rhs(self.h, [cell[v].ctypes.data for v in range(5)], [f.ctypes.data for f in face], 0)
         return cell, face
 
     def step(self, dt: float, nsteps: int = 1):
