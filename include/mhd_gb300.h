@@ -148,6 +148,36 @@ int mhd_cfl_dt(mhd_handle* h, double* dt_out);
 /* max over cells of |div B| = |sum_d (B_d(i_d+1) - B_d(i_d)) / Delta_d|, FP64. */
 int mhd_divb_max(mhd_handle* h, double* out);
 
+/* One RK2 step of one box that allocates no device memory, for callers that
+ * must not call cudaMalloc while they run (a service that reserves its device
+ * memory up front and must not allocate later, a framework whose own pool
+ * accounts for every device byte, a loop that cannot take the device-wide
+ * synchronisation an allocation may cause).  The paper has no counterpart:
+ * it is an interface of this library.
+ *   cell_in/face_in   device arrays of U^n in the state layout (read only);
+ *   cell_out/face_out device arrays that receive U^{n+1} (may not alias the
+ *                     inputs);
+ *   dt > 0: that dt; dt <= 0: the CFL dt of U^n.  *dt_used (may be NULL)
+ *   receives the dt taken.  Work is enqueued on cuda_stream and the call
+ *   synchronises that stream before it returns.
+ * Everything else lives in one static device array of
+ * MHD_NOALLOC_SCRATCH_BYTES, reserved on every GPU that loads the library
+ * until it is unloaded.  A box needs 2*ceil256(8*T*e) + ceil256(8*T*k) +
+ * 2*ceil256(11*N*k) + 512 bytes of it (N cells, T = total state elements, e =
+ * 8 or 4 bytes per state element, k = 8 or 4 per increment / primitive); at
+ * 8 MiB that is up to about 20k cells in FP64 and 40k in FP32 (for example
+ * 24^3 in FP64, 32^3 in FP32).  Larger boxes are rejected with
+ * MHD_ERR_INVALID.  The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture on the device.  All calls share the array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.
+ * Errors: MHD_ERR_INVALID (bad config, null pointer, box too large),
+ * MHD_ERR_CUDA, MHD_ERR_NONFINITE; the text is in mhd_last_error(NULL). */
+#define MHD_NOALLOC_SCRATCH_BYTES (8u << 20)
+int mhd_step_noalloc(const mhd_config* cfg, void* cuda_stream, const void* const cell_in[5],
+                     const void* const face_in[3], void* cell_out[5], void* face_out[3], double dt,
+                     double* dt_used);
+
 /* Counters and the device status word; synchronises. */
 int mhd_get_stats(mhd_handle* h, mhd_stats* out);
 

@@ -1136,3 +1136,11 @@ extern "C" int mhd_batch_autotune(mhd_batch* b, int trial_steps, const char* cac
   if (ms_out) *ms_out = best_ms;
   return MHD_OK;
 }
+
+// Helpers shared with the allocation-free entry point (noalloc.cu).
+namespace mhd {
+int internal_validate(const mhd_config* c) { return validate(c, nullptr); }
+void internal_fill_geo(const mhd_config* c, Geo* g) { fill_geo(c, g); }
+long long internal_face_count(const Geo& g, int d) { return face_count(g, d); }
+void internal_set_error(const char* msg) { g_create_err = msg; }
+}  // namespace mhd

@@ -53,7 +53,7 @@ _VP = C.c_void_p
 _H = C.c_void_p
 EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state", "mhd_step",
            "mhd_step_async", "mhd_rhs", "mhd_set_profiling", "mhd_get_profile", "mhd_cfl_dt", "mhd_divb_max",
-           "mhd_get_stats", "mhd_destroy", "mhd_last_error"]
+           "mhd_get_stats", "mhd_destroy", "mhd_last_error", "mhd_step_noalloc"]
 
 _lib = None
 
@@ -98,6 +98,9 @@ def load(build: bool = True):
     L.mhd_get_stats.argtypes = [_H, C.POINTER(mhd_stats)]
     L.mhd_destroy.restype = None
     L.mhd_destroy.argtypes = [_H]
+    L.mhd_step_noalloc.restype = C.c_int
+    L.mhd_step_noalloc.argtypes = [C.POINTER(mhd_config), _VP, _VP * 5, _VP * 3, _VP * 5, _VP * 3, C.c_double,
+                                   C.POINTER(C.c_double)]
     L.mhd_last_error.restype = C.c_char_p
     L.mhd_last_error.argtypes = [_H]
     _lib = L
@@ -177,6 +180,16 @@ def mhd_get_stats(h) -> dict:
 def mhd_destroy(h):
     if h:
         load().mhd_destroy(h)
+
+
+def mhd_step_noalloc(cfg: mhd_config, cell_in, face_in, cell_out, face_out, dt: float, stream=None) -> float:
+    """One RK2 step that allocates no device memory (see include/mhd_gb300.h).
+    The pointer lists hold device addresses; returns the dt taken."""
+    used = C.c_double(0.0)
+    rc = load().mhd_step_noalloc(C.byref(cfg), _VP(stream or 0), (_VP * 5)(*cell_in), (_VP * 3)(*face_in),
+                                 (_VP * 5)(*cell_out), (_VP * 3)(*face_out), dt, C.byref(used))
+    _check(None, rc)
+    return used.value
 
 
 def mhd_last_error(h=None) -> str:
