@@ -46,8 +46,10 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
-    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--workload", default="turbulence256",
+                   choices=["turbulence256", "ot2d128", "ot3d512", "blast_batch64"])
+    p.add_argument("--precision", default=None, choices=["mixed", "fp64", "fp32"])
+    p.add_argument("--n", type=int, default=None)
     p.add_argument("--tile", default="0,0,0")
     p.add_argument("--compare-steps", type=int, default=10)
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -161,10 +163,40 @@ def cpu_oracle_rate(seconds: float, n: int = 64):
             "sample": f"turbulence_3d recipe at {n}^3, {steps} RK2 steps with CFL dt, single host thread, {el:.1f} s"}
 
 
+WORKLOADS = {
+    "turbulence256": ("mixed", 256),
+    "ot2d128": ("fp64", 128),
+    "ot3d512": ("mixed", 512),
+    "blast_batch64": ("fp32", 64),
+}
+
+
+def resolve(args):
+    prec, n = WORKLOADS[args.workload]
+    args.precision = args.precision or prec
+    args.n = args.n or n
+
+
+def make_box(args):
+    from paper_2606_12753_gb300 import inputs as I
+    if args.workload == "ot2d128":
+        return I.orszag_tang_2d(args.n)
+    if args.workload == "ot3d512":
+        return I.orszag_tang_3d(args.n, seed=12753)
+    return I.turbulence_3d(args.n, seed=2606)
+
+
 def workload_config(args):
-    return {"workload": f"turbulence_3d_{args.n}: 3D decaying MHD turbulence {args.n}^3 periodic, "
-                        f"rho=1 p=0.6 rms Mach 1 beta=1, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
-            "precision": args.precision, "n": args.n}
+    text = {
+        "turbulence256": f"turbulence_3d_{args.n}: 3D decaying MHD turbulence {args.n}^3 periodic, "
+                         f"rho=1 p=0.6 rms Mach 1 beta=1, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
+        "ot2d128": f"orszag_tang_2d_{args.n}: 2D Orszag-Tang {args.n}^2 periodic, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
+        "ot3d512": f"orszag_tang_3d_{args.n}: 3D Orszag-Tang {args.n}^3 periodic (+1% velocity noise), "
+                   f"PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
+        "blast_batch64": f"blast_batch_{args.n}: {args.n} outflow MHD blast boxes, 32-128 cells per axis "
+                         f"log-uniform, one persistent launch per call, autotuned tile, per-box CFL 0.4",
+    }[args.workload]
+    return {"workload": text, "precision": args.precision, "n": args.n}
 
 
 def run_reference(args):
@@ -208,7 +240,7 @@ def run_ours(args):
     from paper_2606_12753_gb300 import mhd
 
     tile = tuple(int(x) for x in args.tile.split(","))
-    box = I.turbulence_3d(args.n, seed=2606)
+    box = make_box(args)
     stream = torch.cuda.Stream()
     solver = mhd.Solver(box, precision=args.precision, tile=tile, stream=stream.cuda_stream)
     solver.set_state(box.cell, box.face)
@@ -249,7 +281,7 @@ def run_ours(args):
     per_launch_ms = stage_ms[k] / max(launches[k], 1)
     alg_bytes = STAGE_BYTES[args.precision][k] * box.ncell
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    tag = f"stage_kernel<{args.precision},{k + 1}>@turbulence_3d_{args.n}"
+    tag = f"stage_kernel<{args.precision},{k + 1}>@{box.name}"
     traffic, src = traffic_from_profiles(tag)
     elem = 4 if args.precision == "fp32" else 8
     kelem = 8 if args.precision == "fp64" else 4
@@ -337,10 +369,68 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """64 independent outflow blast boxes advanced by one persistent launch
+    per call (all K timed steps in one launch, replayed from a CUDA graph)."""
+    import tempfile
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2606_12753_gb300 import inputs as I
+    from paper_2606_12753_gb300 import mhd
+    boxes = I.blast_batch(args.n, seed=64)
+    ncell = sum(b.ncell for b in boxes)
+    stream = torch.cuda.Stream()
+    batch = mhd.Batch(boxes, precision=args.precision, stream=stream.cuda_stream)
+    for i, b in enumerate(boxes):
+        batch.set_state(i, b.cell, b.face)
+    cache = os.environ.get("MHD_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "mhd_autotune.jsonl")
+    tile, tune_ms = batch.autotune(trial_steps=3, cache_path=cache)
+    batch.step(-1.0, args.warmup)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step_async(-1.0, args.steps)
+        e1.record(stream)
+        stream.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    st = batch.stats()
+    if st["status"] != 0:
+        raise RuntimeError(f"device status {st['status']} after the timed steps")
+    value = world * ncell * args.steps / (ms_total / 1e3) / 1e6
+    peak, peak_kind = peaks()
+    step_bytes = sum(STAGE_BYTES[args.precision]) * ncell
+    achieved = step_bytes * args.steps / (ms_total / 1e3) / 1e9
+    (tx, ty, tz), items, grid = batch.tile()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision], "data": "synthetic",
+        "config": {**workload_config(args), "cells": ncell, "tile": [tx, ty, tz], "work_items": items,
+                   "persistent_grid": grid, "autotune_ms_per_step": tune_ms,
+                   "l2": "inputs larger than L2", "parallelism": "single GPU, all boxes in one launch"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": f"batch_kernel<{args.precision},{tx}x{ty}>@blast_batch_{args.n}",
+                     "peak_kind": peak_kind},
+        "gpu_launches": 2 if args.steps else 0,
+        "e2e": None,
+        "clocks": clk.summary(),
+    }
+    batch.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    resolve(args)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "blast_batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

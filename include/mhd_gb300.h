@@ -181,6 +181,56 @@ int mhd_step_noalloc(const mhd_config* cfg, void* cuda_stream, const void* const
 /* Counters and the device status word; synchronises. */
 int mhd_get_stats(mhd_handle* h, mhd_stats* out);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent boxes of uneven size advanced together in ONE
+ * persistent cooperative launch (work items = (box, tile, z-chunk) of the
+ * fused stage kernel; a device-wide barrier between the RK stages), captured
+ * once in a CUDA graph and replayed.  This is the paper's per-step update
+ * (Sec. 2.2) applied to a set of boxes; the batching itself has no
+ * counterpart in the paper.  All boxes share precision, Riemann solver and
+ * EMF mode; sizes, cell sizes and boundary kinds may differ.  Box states use
+ * the single-box layout.
+ * ------------------------------------------------------------------------ */
+typedef struct mhd_batch mhd_batch;
+
+/* Allocate device buffers for nbox boxes described by cfgs[0..nbox-1]; the
+ * tile of cfgs[0] (or the default) is used until mhd_batch_set_tile or
+ * mhd_batch_autotune changes it.  Errors as mhd_create. */
+int mhd_batch_create(int nbox, const mhd_config* cfgs, void* cuda_stream, mhd_batch** out);
+/* Copy the state of box `box` in / out (as mhd_set_state / mhd_get_state). */
+int mhd_batch_set_state(mhd_batch* b, int box, const void* const cell[5], const void* const face[3], int on_device);
+int mhd_batch_get_state(mhd_batch* b, int box, void* cell[5], void* face[3], int on_device);
+/* Advance every box nsteps RK2 steps in one persistent launch.  dt > 0: every
+ * box takes dt; dt <= 0: every box takes its own CFL dt each step.  The
+ * _async form only enqueues; mhd_batch_step synchronises and returns
+ * MHD_ERR_TIMEOUT if the device-wide barrier gave up waiting (after the
+ * timeout set below; the launch then stops, the box states are partially
+ * advanced and the handle stays usable) or MHD_ERR_NONFINITE. */
+int mhd_batch_step(mhd_batch* b, double dt, int nsteps);
+int mhd_batch_step_async(mhd_batch* b, double dt, int nsteps);
+/* Tile (tx, ty: an instantiated shape; tz: planes per z-chunk) of the batch
+ * kernel; get also returns the number of work items and the persistent grid. */
+int mhd_batch_set_tile(mhd_batch* b, int tx, int ty, int tz);
+int mhd_batch_get_tile(mhd_batch* b, int tile[3], long long* items, int* grid);
+/* Time every instantiated tile shape and z-chunk length for trial_steps
+ * steps on this batch (the states are restored afterwards), keep the fastest
+ * and append it to the JSON-lines cache at cache_path (NULL: no cache), keyed
+ * by device, precision, Riemann solver and the box sizes; a cached key is
+ * applied without trials.  tile_out / ms_out (may be NULL) receive the choice
+ * and its time per step. */
+int mhd_batch_autotune(mhd_batch* b, int trial_steps, const char* cache_path, int tile_out[3], double* ms_out);
+/* Limit of every wait at the device-wide barrier (default 2 s). */
+int mhd_batch_set_barrier_timeout(mhd_batch* b, double seconds);
+/* Fault-detection test hook: on = 1 makes CTA 0 skip its first arrival at the
+ * barrier, so the other CTAs run into the timeout; the next step reports
+ * MHD_ERR_TIMEOUT.  No GPU fault is involved. */
+int mhd_batch_inject_missed_arrival(mhd_batch* b, int on);
+/* CFL dt of the current state of box `box`; synchronises. */
+int mhd_batch_box_dt(mhd_batch* b, int box, double* dt_out);
+int mhd_batch_get_stats(mhd_batch* b, mhd_stats* out);
+void mhd_batch_destroy(mhd_batch* b);
+const char* mhd_batch_last_error(const mhd_batch* b);
+
 /* Free every resource of the handle (NULL is a no-op). */
 void mhd_destroy(mhd_handle* h);
 

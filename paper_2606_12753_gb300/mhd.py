@@ -53,7 +53,11 @@ _VP = C.c_void_p
 _H = C.c_void_p
 EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state", "mhd_step",
            "mhd_step_async", "mhd_rhs", "mhd_set_profiling", "mhd_get_profile", "mhd_cfl_dt", "mhd_divb_max",
-           "mhd_get_stats", "mhd_destroy", "mhd_last_error", "mhd_step_noalloc"]
+           "mhd_get_stats", "mhd_destroy", "mhd_last_error", "mhd_step_noalloc",
+           "mhd_batch_create", "mhd_batch_set_state", "mhd_batch_get_state", "mhd_batch_step",
+           "mhd_batch_step_async", "mhd_batch_set_tile", "mhd_batch_get_tile", "mhd_batch_autotune",
+           "mhd_batch_set_barrier_timeout", "mhd_batch_inject_missed_arrival", "mhd_batch_box_dt",
+           "mhd_batch_get_stats", "mhd_batch_destroy", "mhd_batch_last_error"]
 
 _lib = None
 
@@ -101,6 +105,32 @@ def load(build: bool = True):
     L.mhd_step_noalloc.restype = C.c_int
     L.mhd_step_noalloc.argtypes = [C.POINTER(mhd_config), _VP, _VP * 5, _VP * 3, _VP * 5, _VP * 3, C.c_double,
                                    C.POINTER(C.c_double)]
+    L.mhd_batch_create.restype = C.c_int
+    L.mhd_batch_create.argtypes = [C.c_int, C.POINTER(mhd_config), _VP, C.POINTER(_H)]
+    for name in ("mhd_batch_set_state", "mhd_batch_get_state"):
+        getattr(L, name).restype = C.c_int
+        getattr(L, name).argtypes = [_H, C.c_int, _VP * 5, _VP * 3, C.c_int]
+    for name in ("mhd_batch_step", "mhd_batch_step_async"):
+        getattr(L, name).restype = C.c_int
+        getattr(L, name).argtypes = [_H, C.c_double, C.c_int]
+    L.mhd_batch_set_tile.restype = C.c_int
+    L.mhd_batch_set_tile.argtypes = [_H, C.c_int, C.c_int, C.c_int]
+    L.mhd_batch_get_tile.restype = C.c_int
+    L.mhd_batch_get_tile.argtypes = [_H, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+    L.mhd_batch_autotune.restype = C.c_int
+    L.mhd_batch_autotune.argtypes = [_H, C.c_int, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.mhd_batch_set_barrier_timeout.restype = C.c_int
+    L.mhd_batch_set_barrier_timeout.argtypes = [_H, C.c_double]
+    L.mhd_batch_inject_missed_arrival.restype = C.c_int
+    L.mhd_batch_inject_missed_arrival.argtypes = [_H, C.c_int]
+    L.mhd_batch_box_dt.restype = C.c_int
+    L.mhd_batch_box_dt.argtypes = [_H, C.c_int, C.POINTER(C.c_double)]
+    L.mhd_batch_get_stats.restype = C.c_int
+    L.mhd_batch_get_stats.argtypes = [_H, C.POINTER(mhd_stats)]
+    L.mhd_batch_destroy.restype = None
+    L.mhd_batch_destroy.argtypes = [_H]
+    L.mhd_batch_last_error.restype = C.c_char_p
+    L.mhd_batch_last_error.argtypes = [_H]
     L.mhd_last_error.restype = C.c_char_p
     L.mhd_last_error.argtypes = [_H]
     _lib = L
@@ -284,6 +314,111 @@ class Solver:
     def close(self):
         if self.h:
             mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batches ---------------------------------------------------------------
+
+def _bcheck(b, rc):
+    if rc != MHD_OK:
+        msg = load().mhd_batch_last_error(b)
+        raise MHDError(rc, msg.decode() if msg else "")
+
+
+def box_config(box, precision="fp32", riemann="hlld", emf="upwind", tile=(0, 0, 0), cfl=None):
+    c = mhd_default_config(box.nx, box.ny, box.nz)
+    c.dx, c.dy, c.dz = box.dx, box.dy, box.dz
+    c.gamma = box.gamma
+    c.cfl = cfl if cfl is not None else getattr(box, "cfl", 0.4)
+    c.bc = (C.c_int * 3)(*box.bc)
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+    c.riemann = RIEMANN[riemann] if isinstance(riemann, str) else riemann
+    c.emf = MHD_EMF_MEAN if emf == "mean" else MHD_EMF_UPWIND
+    c.tile_x, c.tile_y, c.tile_z = tile
+    return c
+
+
+class Batch:
+    """Many boxes advanced in one persistent launch (``mhd_batch_*``)."""
+
+    def __init__(self, boxes, precision="fp32", riemann="hlld", emf="upwind", tile=(0, 0, 0), stream=None):
+        cfgs = (mhd_config * len(boxes))(*[box_config(b, precision, riemann, emf, tile) for b in boxes])
+        h = _H()
+        _bcheck(None, load().mhd_batch_create(len(boxes), cfgs, _VP(stream or 0), C.byref(h)))
+        self.h = h
+        self.boxes = boxes
+        self.cfgs = cfgs
+        self.dtype = np.float32 if cfgs[0].precision == MHD_FP32 else np.float64
+
+    def _shapes(self, i):
+        b = self.boxes[i]
+        o = [1 if x == MHD_BC_OUTFLOW else 0 for x in b.bc]
+        return (5, b.nz, b.ny, b.nx), [(b.nz, b.ny, b.nx + o[0]), (b.nz, b.ny + o[1], b.nx), (b.nz + o[2], b.ny, b.nx)]
+
+    def set_state(self, i, cell, face):
+        cs, fs = self._shapes(i)
+        c = np.ascontiguousarray(cell, dtype=self.dtype)
+        f = [np.ascontiguousarray(x, dtype=self.dtype) for x in face]
+        assert c.shape == cs and [x.shape for x in f] == fs
+        _bcheck(self.h, load().mhd_batch_set_state(self.h, i, (_VP * 5)(*[c[v].ctypes.data for v in range(5)]),
+                                                   (_VP * 3)(*[x.ctypes.data for x in f]), 0))
+
+    def get_state(self, i):
+        cs, fs = self._shapes(i)
+        c = np.empty(cs, dtype=self.dtype)
+        f = [np.empty(s, dtype=self.dtype) for s in fs]
+        _bcheck(self.h, load().mhd_batch_get_state(self.h, i, (_VP * 5)(*[c[v].ctypes.data for v in range(5)]),
+                                                   (_VP * 3)(*[x.ctypes.data for x in f]), 0))
+        return c, f
+
+    def step(self, dt, nsteps=1):
+        _bcheck(self.h, load().mhd_batch_step(self.h, dt, nsteps))
+
+    def step_async(self, dt, nsteps=1):
+        _bcheck(self.h, load().mhd_batch_step_async(self.h, dt, nsteps))
+
+    def set_tile(self, tx, ty, tz):
+        _bcheck(self.h, load().mhd_batch_set_tile(self.h, tx, ty, tz))
+
+    def tile(self):
+        t = (C.c_int * 3)()
+        items = C.c_longlong()
+        grid = C.c_int()
+        _bcheck(self.h, load().mhd_batch_get_tile(self.h, t, C.byref(items), C.byref(grid)))
+        return (t[0], t[1], t[2]), items.value, grid.value
+
+    def autotune(self, trial_steps=3, cache_path=None):
+        t = (C.c_int * 3)()
+        ms = C.c_double()
+        _bcheck(self.h, load().mhd_batch_autotune(self.h, trial_steps, cache_path.encode() if cache_path else None,
+                                                  t, C.byref(ms)))
+        return (t[0], t[1], t[2]), ms.value
+
+    def set_barrier_timeout(self, seconds):
+        _bcheck(self.h, load().mhd_batch_set_barrier_timeout(self.h, seconds))
+
+    def inject_missed_arrival(self, on=True):
+        _bcheck(self.h, load().mhd_batch_inject_missed_arrival(self.h, 1 if on else 0))
+
+    def box_dt(self, i):
+        out = C.c_double()
+        _bcheck(self.h, load().mhd_batch_box_dt(self.h, i, C.byref(out)))
+        return out.value
+
+    def stats(self):
+        s = mhd_stats()
+        _bcheck(self.h, load().mhd_batch_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in mhd_stats._fields_}
+
+    def close(self):
+        if self.h:
+            load().mhd_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -20,15 +20,22 @@ def rel_l1(q, ref, floor=0.0):
 
 def state_errors(cell, face, ref_cell, ref_face):
     """Per-variable relative L1 errors.  A vector component is measured
-    against max(its own L1 norm, 1e-3 x the L1 norm of the whole vector), so a
-    component that is zero up to rounding (v_z, B_z of a 2D problem) is not
-    divided by its own rounding noise."""
+    against max(its own L1 norm, 1e-3 x the L1 norm of the whole vector,
+    1e-4 x an energy scale of that vector: sum sqrt(rho E) for momentum,
+    sum sqrt(E) for the field), so a component that is zero up to rounding
+    (v_z, B_z of a 2D problem, the momentum of a box at rest) is not divided by
+    its own rounding noise."""
     names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz"]
-    mnorm = float(np.abs(np.asarray(ref_cell[1:4], dtype=np.float64)).sum())
+    rc = np.asarray(ref_cell, dtype=np.float64)
+    mnorm = float(np.abs(rc[1:4]).sum())
     bnorm = float(sum(np.abs(np.asarray(f, dtype=np.float64)).sum() for f in ref_face))
+    e_pos = np.maximum(rc[4], 0.0)
+    m_scale = float(np.sqrt(np.maximum(rc[0], 0.0) * e_pos).sum())
+    b_scale = float(np.sqrt(e_pos).sum())
     errs = {}
     for v in range(5):
-        errs[names[v]] = rel_l1(cell[v], ref_cell[v], 1e-3 * mnorm if 1 <= v <= 3 else 0.0)
+        floor = max(1e-3 * mnorm, 1e-4 * m_scale) if 1 <= v <= 3 else 0.0
+        errs[names[v]] = rel_l1(cell[v], ref_cell[v], floor)
     for d in range(3):
-        errs[names[5 + d]] = rel_l1(face[d], ref_face[d], 1e-3 * bnorm)
+        errs[names[5 + d]] = rel_l1(face[d], ref_face[d], max(1e-3 * bnorm, 1e-4 * b_scale))
     return errs
