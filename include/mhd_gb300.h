@@ -182,6 +182,46 @@ int mhd_step_noalloc(const mhd_config* cfg, void* cuda_stream, const void* const
 int mhd_get_stats(mhd_handle* h, mhd_stats* out);
 
 /* ------------------------------------------------------------------------
+ * Learned HLL/HLLD face switch.  A network 16 -> 32 -> 32 -> 1 (ReLU, ReLU,
+ * sigmoid) predicts per face whether the cheap HLL flux suffices or the HLLD
+ * flux is needed; HLLD stays the fallback and every flux is still one of the
+ * two solvers (the flux arithmetic itself is never replaced).  The paper names
+ * both solvers (Sec. 2.2, HLLD_Solver and HLL_Solver in Tables 2-4); the
+ * network is this library's addition.  Inference and training use BF16
+ * tensor-core MMAs with FP32 accumulation.
+ *
+ * Parameter block: mlp_param_bytes() bytes of device memory, caller-owned:
+ * FP32 master parameters in the order W1[32][16], b1[32], W2[32][32], b2[32],
+ * W3[32], b3 (1633 values), followed by the bf16 copies of W1, W2, W3.
+ * Features: 16 floats per face (see mhd_dump_faces); logits: 1 float.
+ * All array arguments are device pointers; calls enqueue on cuda_stream.
+ * ------------------------------------------------------------------------ */
+size_t mlp_param_bytes(void);
+/* Copy 1633 host FP32 parameters into a block and derive its bf16 copies (synchronises). */
+int mlp_init(void* block, const float* master_host, void* cuda_stream);
+/* logits[i] of the n feature rows. */
+int mlp_forward(const void* block, const float* features, long long n, float* logits, void* cuda_stream);
+/* Add to grad[1633] the gradient of the mean binary cross-entropy of the n rows
+ * against labels (0/1); the caller zeroes grad. */
+int mlp_backward(const void* block, const float* features, const float* labels, long long n, float* grad,
+                 void* cuda_stream);
+/* One Adam step (step = 1, 2, ...) on the master parameters with moments m, v
+ * (1633 floats each, zero-initialised by the caller); refreshes the bf16 copies. */
+int mlp_adam(void* block, float* m, float* v, const float* grad, int step, double lr, double beta1, double beta2,
+             double eps, void* cuda_stream);
+/* Training data from the current state of a periodic box: for each face id
+ * (d * nx*ny*nz + cell index, the face below that cell along axis d) the 16
+ * features of its reconstructed states and the label 1 when the HLLD and HLL
+ * fluxes differ by more than 1e-3 in some scaled component (scores, may be
+ * NULL: that largest scaled difference).  Synchronises. */
+int mhd_dump_faces(mhd_handle* h, const long long* face_ids, long long n, float* features, float* labels,
+                   float* scores);
+/* Use the network in `block` (device, copied) to choose the solver of every
+ * face when the handle's riemann is MHD_LEARNED: HLLD when sigmoid(logit) >=
+ * tau, HLL otherwise. */
+int mhd_set_switch(mhd_handle* h, const void* block, double tau);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent boxes of uneven size advanced together in ONE
  * persistent cooperative launch (work items = (box, tile, z-chunk) of the
  * fused stage kernel; a device-wide barrier between the RK stages), captured

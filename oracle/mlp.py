@@ -107,8 +107,11 @@ def bce_loss(z, y):
     return float(np.mean(np.maximum(z, 0.0) - z * y + np.log1p(np.exp(-np.abs(z)))))
 
 
-def backward(cache, z, y):
-    """Gradients of the mean BCE loss with respect to every parameter."""
+def backward(cache, z, y, bf16_deltas=False):
+    """Gradients of the mean BCE loss with respect to every parameter.  With
+    bf16_deltas the layer deltas are rounded to bfloat16 where they enter a
+    matrix product (as tensor-core operands); bias sums use them unrounded."""
+    r = bf16 if bf16_deltas else (lambda a: a)
     n = z.shape[0]
     dz = (sigmoid(z) - y) / n                       # (N,)
     g = {}
@@ -116,11 +119,11 @@ def backward(cache, z, y):
     g["b3"] = np.array([dz.sum()])
     dh2 = dz[:, None] * cache["W3"]                  # (N, 32)
     da2 = dh2 * (cache["a2"] > 0.0)
-    g["W2"] = da2.T @ cache["h1"]
+    g["W2"] = r(da2).T @ cache["h1"]
     g["b2"] = da2.sum(axis=0)
-    dh1 = da2 @ cache["W2"]
+    dh1 = r(da2) @ cache["W2"]
     da1 = dh1 * (cache["a1"] > 0.0)
-    g["W1"] = da1.T @ cache["X"]
+    g["W1"] = r(da1).T @ cache["X"]
     g["b1"] = da1.sum(axis=0)
     return g
 

@@ -83,6 +83,8 @@ struct mhd_handle {
   double last_dt = 0.0;
   int steps = 0;
   bool profiling = false;
+  void* mlp = nullptr;                     // copy of the switch network (device)
+  float mlp_tau = 0.5f;
   std::vector<cudaEvent_t> ev_pool;        // 3 events per recorded step
   size_t ev_used = 0;
   std::string err;
@@ -257,6 +259,7 @@ extern "C" void mhd_destroy(mhd_handle* h) {
   cudaFree(h->W[0]);
   cudaFree(h->W[1]);
   cudaFree(h->words);
+  cudaFree(h->mlp);
   if (h->pinned) cudaFreeHost(h->pinned);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -315,6 +318,8 @@ static StageArgs base_args(mhd_handle* h) {
   memset(&a, 0, sizeof a);
   a.status = h->status;
   a.counters = h->counters;
+  a.mlp = (const float*)h->mlp;
+  a.mlp_tau = h->mlp_tau;
   return a;
 }
 
@@ -1144,3 +1149,37 @@ void internal_fill_geo(const mhd_config* c, Geo* g) { fill_geo(c, g); }
 long long internal_face_count(const Geo& g, int d) { return face_count(g, d); }
 void internal_set_error(const char* msg) { g_create_err = msg; }
 }  // namespace mhd
+
+// ---------------------------------------------------------------- learned switch
+namespace mhd {
+int dump_faces_launch(int prec, const Geo& g, const void* W, const long long* ids, long long n, float* X, float* y,
+                      float* score, cudaStream_t st);
+}
+extern "C" size_t mlp_param_bytes(void);
+
+extern "C" int mhd_dump_faces(mhd_handle* h, const long long* face_ids, long long n, float* features, float* labels,
+                              float* scores) {
+  if (!h) return MHD_ERR_INVALID;
+  if (!face_ids || !features || !labels || n < 0) return fail(h, MHD_ERR_INVALID, "bad arguments");
+  for (int d = 0; d < 3; ++d)
+    if (h->geo.bc[d] != 0) return fail(h, MHD_ERR_INVALID, "mhd_dump_faces samples periodic boxes only");
+  cudaError_t e = ensure_prims(h);
+  if (e) return fail(h, MHD_ERR_CUDA, "primitive recovery failed: %s", cudaGetErrorString(e));
+  if (n == 0) return MHD_OK;
+  int rc = dump_faces_launch(h->cfg.precision, h->geo, h->W[h->cur], face_ids, n, features, labels, scores,
+                             h->stream);
+  if (rc) return fail(h, rc, "face sampler launch failed");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MHD_OK;
+}
+
+extern "C" int mhd_set_switch(mhd_handle* h, const void* block, double tau) {
+  if (!h) return MHD_ERR_INVALID;
+  if (!block) return fail(h, MHD_ERR_INVALID, "null parameter block");
+  if (!(tau > 0.0 && tau < 1.0)) return fail(h, MHD_ERR_INVALID, "tau must lie in (0, 1)");
+  if (!h->mlp) CUDA_TRY(h, cudaMalloc(&h->mlp, mlp_param_bytes()));
+  CUDA_TRY(h, cudaMemcpyAsync(h->mlp, block, mlp_param_bytes(), cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->mlp_tau = (float)tau;
+  return MHD_OK;
+}

@@ -57,7 +57,9 @@ EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state",
            "mhd_batch_create", "mhd_batch_set_state", "mhd_batch_get_state", "mhd_batch_step",
            "mhd_batch_step_async", "mhd_batch_set_tile", "mhd_batch_get_tile", "mhd_batch_autotune",
            "mhd_batch_set_barrier_timeout", "mhd_batch_inject_missed_arrival", "mhd_batch_box_dt",
-           "mhd_batch_get_stats", "mhd_batch_destroy", "mhd_batch_last_error"]
+           "mhd_batch_get_stats", "mhd_batch_destroy", "mhd_batch_last_error",
+           "mlp_param_bytes", "mlp_init", "mlp_forward", "mlp_backward", "mlp_adam", "mhd_dump_faces",
+           "mhd_set_switch"]
 
 _lib = None
 
@@ -131,6 +133,20 @@ def load(build: bool = True):
     L.mhd_batch_destroy.argtypes = [_H]
     L.mhd_batch_last_error.restype = C.c_char_p
     L.mhd_batch_last_error.argtypes = [_H]
+    L.mlp_param_bytes.restype = C.c_size_t
+    L.mlp_param_bytes.argtypes = []
+    L.mlp_init.restype = C.c_int
+    L.mlp_init.argtypes = [_VP, C.POINTER(C.c_float), _VP]
+    L.mlp_forward.restype = C.c_int
+    L.mlp_forward.argtypes = [_VP, _VP, C.c_longlong, _VP, _VP]
+    L.mlp_backward.restype = C.c_int
+    L.mlp_backward.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, _VP]
+    L.mlp_adam.restype = C.c_int
+    L.mlp_adam.argtypes = [_VP, _VP, _VP, _VP, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _VP]
+    L.mhd_dump_faces.restype = C.c_int
+    L.mhd_dump_faces.argtypes = [_H, _VP, C.c_longlong, _VP, _VP, _VP]
+    L.mhd_set_switch.restype = C.c_int
+    L.mhd_set_switch.argtypes = [_H, _VP, C.c_double]
     L.mhd_last_error.restype = C.c_char_p
     L.mhd_last_error.argtypes = [_H]
     _lib = L
@@ -426,3 +442,45 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- learned face switch ------------------------------------------------------
+
+MLP_NPARAM = 1633
+
+
+def mlp_param_bytes() -> int:
+    return int(load().mlp_param_bytes())
+
+
+def _rc(rc, what):
+    if rc != MHD_OK:
+        raise MHDError(rc, what)
+
+
+def mlp_init(block_ptr, master_host: np.ndarray, stream=None):
+    m = np.ascontiguousarray(master_host, dtype=np.float32)
+    assert m.size == MLP_NPARAM
+    _rc(load().mlp_init(_VP(block_ptr), m.ctypes.data_as(C.POINTER(C.c_float)), _VP(stream or 0)), "mlp_init")
+
+
+def mlp_forward(block_ptr, x_ptr, n, z_ptr, stream=None):
+    _rc(load().mlp_forward(_VP(block_ptr), _VP(x_ptr), n, _VP(z_ptr), _VP(stream or 0)), "mlp_forward")
+
+
+def mlp_backward(block_ptr, x_ptr, y_ptr, n, grad_ptr, stream=None):
+    _rc(load().mlp_backward(_VP(block_ptr), _VP(x_ptr), _VP(y_ptr), n, _VP(grad_ptr), _VP(stream or 0)),
+        "mlp_backward")
+
+
+def mlp_adam(block_ptr, m_ptr, v_ptr, grad_ptr, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _rc(load().mlp_adam(_VP(block_ptr), _VP(m_ptr), _VP(v_ptr), _VP(grad_ptr), step, lr, beta1, beta2, eps,
+                        _VP(stream or 0)), "mlp_adam")
+
+
+def mhd_dump_faces(h, ids_ptr, n, x_ptr, y_ptr, score_ptr=None):
+    _check(h, load().mhd_dump_faces(h, _VP(ids_ptr), n, _VP(x_ptr), _VP(y_ptr), _VP(score_ptr or 0)))
+
+
+def mhd_set_switch(h, block_ptr, tau):
+    _check(h, load().mhd_set_switch(h, _VP(block_ptr), tau))
