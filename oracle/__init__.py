@@ -30,7 +30,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 PERIODIC, OUTFLOW = 0, 1
-HLLD, HLL = 0, 1
+HLLD, HLL, LEARNED, MASK = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -50,11 +50,14 @@ class _Cfg(C.Structure):
                 ("gamma", C.c_double), ("cfl", C.c_double),
                 ("bc", C.c_int * 3),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
-                ("emf_mean", C.c_int), ("riemann", C.c_int)]
+                ("emf_mean", C.c_int), ("riemann", C.c_int),
+                ("mlp", C.POINTER(C.c_double)), ("mlp_zt", C.c_double),
+                ("choice", C.POINTER(C.c_ubyte))]
 
 
 class _Stats(C.Structure):
-    _fields_ = [("rho_floor_hits", C.c_longlong), ("p_floor_hits", C.c_longlong)]
+    _fields_ = [("rho_floor_hits", C.c_longlong), ("p_floor_hits", C.c_longlong),
+                ("faces_hll", C.c_longlong), ("faces_hlld", C.c_longlong)]
 
 
 @dataclass
@@ -73,11 +76,31 @@ class Config:
     p_floor: float = 1e-10
     emf_mean: int = 0
     riemann: int = HLLD
+    # LEARNED: the 1633 network parameters (oracle/mlp.py order) and the logit
+    # threshold (HLLD when logit >= mlp_zt); MASK: per-face choices (uint8,
+    # 1 = HLLD) indexed d * nx*ny*nz + cell
+    mlp: np.ndarray | None = None
+    mlp_zt: float = 0.0
+    choice: np.ndarray | None = None
 
     def c(self) -> _Cfg:
+        mp = None
+        if self.mlp is not None:
+            self.mlp = np.ascontiguousarray(self.mlp, dtype=np.float64)
+            assert self.mlp.size == 1633
+            mp = self.mlp.ctypes.data_as(C.POINTER(C.c_double))
+        cp = None
+        if self.choice is not None:
+            self.choice = np.ascontiguousarray(self.choice, dtype=np.uint8)
+            assert self.choice.size == 3 * self.nx * self.ny * self.nz
+            cp = self.choice.ctypes.data_as(C.POINTER(C.c_ubyte))
+        if self.riemann == LEARNED:
+            assert mp is not None, "LEARNED needs the network parameters"
+        if self.riemann == MASK:
+            assert cp is not None, "MASK needs the per-face choices"
         return _Cfg(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.gamma, self.cfl,
                     (C.c_int * 3)(*self.bc), self.rho_floor, self.p_floor, self.emf_mean,
-                    self.riemann)
+                    self.riemann, mp, self.mlp_zt, cp)
 
     def face_shapes(self):
         o = [1 if b == OUTFLOW else 0 for b in self.bc]
@@ -114,6 +137,14 @@ def lib():
         L.orc_cfl_dt.argtypes = [C.POINTER(_Cfg), PP, PF]
         L.orc_divb_max.restype = C.c_double
         L.orc_divb_max.argtypes = [C.POINTER(_Cfg), PF]
+        L.orc_bf16.restype = C.c_double
+        L.orc_bf16.argtypes = [C.c_double]
+        L.orc_features.restype = None
+        L.orc_features.argtypes = [_P, _P, C.c_double, C.c_double, _P]
+        L.orc_mlp_logit.restype = C.c_double
+        L.orc_mlp_logit.argtypes = [_P, _P]
+        L.orc_switch_logits.restype = None
+        L.orc_switch_logits.argtypes = [C.POINTER(_Cfg), PP, PF, _P]
         _lib = L
     return _lib
 
@@ -166,6 +197,14 @@ def hll(wl, wr, bn: float, gamma: float) -> np.ndarray:
 class Stats:
     rho_floor_hits: int = 0
     p_floor_hits: int = 0
+    faces_hll: int = 0
+    faces_hlld: int = 0
+
+    def add(self, st):
+        self.rho_floor_hits += st.rho_floor_hits
+        self.p_floor_hits += st.p_floor_hits
+        self.faces_hll += st.faces_hll
+        self.faces_hlld += st.faces_hlld
 
 
 def _state_ptrs(cfg: Config, cell: np.ndarray, face):
@@ -187,7 +226,7 @@ def step(cfg: Config, cell, face, dt: float, nsteps: int = 1, stats: Stats | Non
     step).  Returns new (cell, face, dts); the inputs are left untouched."""
     cell, face = copy_state(cell, face)
     c = cfg.c()
-    st = _Stats(0, 0)
+    st = _Stats(0, 0, 0, 0)
     cp, fp = _state_ptrs(cfg, cell, face)
     dts = []
     for _ in range(nsteps):
@@ -195,8 +234,7 @@ def step(cfg: Config, cell, face, dt: float, nsteps: int = 1, stats: Stats | Non
         lib().orc_step(C.byref(c), cp, fp, h, C.byref(st))
         dts.append(h)
     if stats is not None:
-        stats.rho_floor_hits += st.rho_floor_hits
-        stats.p_floor_hits += st.p_floor_hits
+        stats.add(st)
     return cell, face, dts
 
 
@@ -216,14 +254,44 @@ def rhs(cfg: Config, cell, face, stats: Stats | None = None):
     du = np.zeros_like(cell)
     db = [np.zeros_like(f) for f in face]
     c = cfg.c()
-    st = _Stats(0, 0)
+    st = _Stats(0, 0, 0, 0)
     cp, fp = _state_ptrs(cfg, cell, face)
     dp, dbp = _state_ptrs(cfg, du, db)
     lib().orc_rhs(C.byref(c), cp, fp, dp, dbp, C.byref(st))
     if stats is not None:
-        stats.rho_floor_hits += st.rho_floor_hits
-        stats.p_floor_hits += st.p_floor_hits
+        stats.add(st)
     return du, db
+
+
+def bf16(x: float) -> float:
+    """Nearest bfloat16 of x (rounded to binary32 first), ties to even."""
+    return lib().orc_bf16(float(x))
+
+
+def switch_features(wl, wr, bn: float, gamma: float) -> np.ndarray:
+    """The 16 features of the learned switch (C restatement)."""
+    wl, wr = _vec(wl, 7), _vec(wr, 7)
+    f = np.zeros(16)
+    lib().orc_features(_ptr(wl), _ptr(wr), bn, gamma, _ptr(f))
+    return f
+
+
+def switch_logit(params, f) -> float:
+    """Logit of the switch network (bf16 inputs, weights and activations, FP64 sums)."""
+    p = _vec(params, 1633)
+    f = _vec(f, 16)
+    return lib().orc_mlp_logit(_ptr(p), _ptr(f))
+
+
+def switch_logits(cfg: Config, cell, face) -> np.ndarray:
+    """LEARNED: the network's logit on every cell's lower face, shape (3, nz, ny, nx)."""
+    assert cfg.riemann == LEARNED
+    cell, face = copy_state(cell, face)
+    c = cfg.c()
+    cp, fp = _state_ptrs(cfg, cell, face)
+    z = np.zeros((3, cfg.nz, cfg.ny, cfg.nx))
+    lib().orc_switch_logits(C.byref(c), cp, fp, _ptr(z))
+    return z
 
 
 def cfl_dt(cfg: Config, cell, face) -> float:

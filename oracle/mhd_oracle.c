@@ -51,6 +51,8 @@
 #define ORC_OUTFLOW 1
 #define ORC_HLLD 0
 #define ORC_HLL 1
+#define ORC_LEARNED 2   /* per face: the switch network below picks HLL or HLLD */
+#define ORC_MASK 3      /* per face: the choice is an input (cfg->choice) */
 
 typedef struct {
   int nx, ny, nz;
@@ -59,12 +61,20 @@ typedef struct {
   int bc[3];
   double rho_floor, p_floor;
   int emf_mean;     /* 0: Gardiner-Stone upwind contact average, 1: plain mean */
-  int riemann;      /* ORC_HLLD or ORC_HLL */
+  int riemann;      /* ORC_HLLD, ORC_HLL, ORC_LEARNED or ORC_MASK */
+  const double *mlp;          /* ORC_LEARNED: the 1633 network parameters W1[32][16], b1[32],
+                                 W2[32][32], b2[32], W3[32], b3 */
+  double mlp_zt;              /* ORC_LEARNED: HLLD when the logit >= mlp_zt (or is NaN) */
+  const unsigned char *choice; /* ORC_MASK: 1 = HLLD, 0 = HLL for the lower face of interior
+                                  cell s along d at [d * nx*ny*nz + s]; ghost faces take the
+                                  choice of the cell they wrap to (periodic boxes) */
 } orc_cfg;
 
 typedef struct {
   long long rho_floor_hits;
   long long p_floor_hits;
+  long long faces_hll;    /* faces of interior cells solved with HLL ... */
+  long long faces_hlld;   /* ... and with HLLD, per operator evaluation */
 } orc_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -250,6 +260,72 @@ void orc_hlld(const double *wl, const double *wr, double bn, double gamma, doubl
 /* grid with explicit ghost layers                                           */
 /* ------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------ */
+/* learned HLL/HLLD switch: features and network (the library's addition to  */
+/* the method; the paper names the two solvers, Sec. 2.2, Tables 2-4)        */
+/* ------------------------------------------------------------------------ */
+
+/* Nearest bfloat16 (ties to even) of x first rounded to binary32. */
+double orc_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  memcpy(&f, &u, sizeof f);
+  return (double)f;
+}
+
+/* The 16 dimensionless features of a face from its reconstructed states
+ * (rho, v_n, v_t1, v_t2, p, B_t1, B_t2), with rho_bar = (rho_L+rho_R)/2,
+ * p_bar = (p_L+p_R)/2, c = max(c_fL, c_fR), b = sqrt(rho_bar) c:
+ * rho_L/rho_bar, rho_R/rho_bar, v_L/c (3), v_R/c (3), p_L/p_bar, p_R/p_bar,
+ * B_n/b, B_tL/b (2), B_tR/b (2), min(c_fL, c_fR)/c. */
+void orc_features(const double *wl, const double *wr, double bn, double gamma, double *f) {
+  double cl = orc_fast_speed(wl, bn, gamma), cr = orc_fast_speed(wr, bn, gamma);
+  double rho = 0.5 * (wl[0] + wr[0]);
+  double pbar = 0.5 * (wl[4] + wr[4]);
+  double c = cl > cr ? cl : cr;
+  double b = sqrt(rho) * c;
+  f[0] = wl[0] / rho;
+  f[1] = wr[0] / rho;
+  for (int v = 0; v < 3; ++v) {
+    f[2 + v] = wl[1 + v] / c;
+    f[5 + v] = wr[1 + v] / c;
+  }
+  f[8] = wl[4] / pbar;
+  f[9] = wr[4] / pbar;
+  f[10] = bn / b;
+  f[11] = wl[5] / b;
+  f[12] = wl[6] / b;
+  f[13] = wr[5] / b;
+  f[14] = wr[6] / b;
+  f[15] = (cl < cr ? cl : cr) / c;
+}
+
+/* Logit of the network 16 -> 32 -> 32 -> 1 (ReLU hidden layers) as the
+ * tensor cores see it: features, weights and hidden activations rounded to
+ * bfloat16, biases as given, every sum in FP64. */
+double orc_mlp_logit(const double *prm, const double *f) {
+  const double *W1 = prm, *b1 = prm + 512, *W2 = prm + 544, *b2 = prm + 1568, *W3 = prm + 1600, *b3 = prm + 1632;
+  double x[16], h1[32], h2[32];
+  for (int i = 0; i < 16; ++i) x[i] = orc_bf16(f[i]);
+  for (int o = 0; o < 32; ++o) {
+    double a = 0.0;
+    for (int i = 0; i < 16; ++i) a += orc_bf16(W1[o * 16 + i]) * x[i];
+    a += b1[o];
+    h1[o] = orc_bf16(a > 0.0 ? a : 0.0);
+  }
+  for (int o = 0; o < 32; ++o) {
+    double a = 0.0;
+    for (int i = 0; i < 32; ++i) a += orc_bf16(W2[o * 32 + i]) * h1[i];
+    a += b2[o];
+    h2[o] = orc_bf16(a > 0.0 ? a : 0.0);
+  }
+  double z = 0.0;
+  for (int i = 0; i < 32; ++i) z += orc_bf16(W3[i]) * h2[i];
+  return z + b3[0];
+}
+
 typedef struct {
   const orc_cfg *c;
   int n[3];      /* interior cells */
@@ -257,6 +333,8 @@ typedef struct {
   int nf[3];     /* stored faces along each normal: n (periodic) or n+1 */
   size_t ncell;  /* extended cell count */
   size_t nedge;  /* (N+1)^3 style count for face/edge arrays */
+  orc_stats *st;
+  double *zout;  /* ORC_LEARNED: logits of the interior cells' lower faces, or NULL */
 } grid;
 
 static size_t cidx(const grid *g, int I, int J, int K) {
@@ -425,9 +503,32 @@ static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7
         if (wl[4] < c->p_floor) wl[4] = c->p_floor;
         if (wr[4] < c->p_floor) wr[4] = c->p_floor;
         double bn = Bf[d][fidx(g, I, J, K)];
+        /* interior cell whose lower face this is (periodic wrap; outflow clamp) */
+        int ii = I - NG, jj = J - NG, kk = K - NG;
+        int interior = ii >= 0 && ii < g->n[0] && jj >= 0 && jj < g->n[1] && kk >= 0 && kk < g->n[2];
+        size_t s_own = (size_t)wrap_or_clamp(ii, g->n[0], c->bc[0]) +
+                       (size_t)g->n[0] * ((size_t)wrap_or_clamp(jj, g->n[1], c->bc[1]) +
+                                          (size_t)g->n[1] * (size_t)wrap_or_clamp(kk, g->n[2], c->bc[2]));
+        size_t nint = (size_t)g->n[0] * g->n[1] * g->n[2];
+        int use_hlld = 1;
+        if (c->riemann == ORC_HLL) {
+          use_hlld = 0;
+        } else if (c->riemann == ORC_LEARNED) {
+          double feat[16];
+          orc_features(wl, wr, bn, c->gamma, feat);
+          double z = orc_mlp_logit(c->mlp, feat);
+          use_hlld = !(z < c->mlp_zt);
+          if (g->zout && interior) g->zout[(size_t)d * nint + s_own] = z;
+        } else if (c->riemann == ORC_MASK) {
+          use_hlld = c->choice[(size_t)d * nint + s_own] != 0;
+        }
         double f[7];
-        if (c->riemann == ORC_HLL) orc_hll(wl, wr, bn, c->gamma, f);
-        else orc_hlld(wl, wr, bn, c->gamma, f);
+        if (use_hlld) orc_hlld(wl, wr, bn, c->gamma, f);
+        else orc_hll(wl, wr, bn, c->gamma, f);
+        if (interior && g->st) {
+          if (use_hlld) g->st->faces_hlld++;
+          else g->st->faces_hll++;
+        }
         size_t fq = fidx(g, I, J, K);
         for (int v = 0; v < 7; ++v) F[v][fq] = f[v];
         double cl = orc_fast_speed(wl, bn, c->gamma), cr = orc_fast_speed(wr, bn, c->gamma);
@@ -447,9 +548,11 @@ static double upwind(double mflux, double lo, double hi) {
 /* full spatial operator: dU (5 cell arrays) and dB (3 face arrays) in the
  * caller's storage layout. */
 static void spatial_operator(const orc_cfg *c, double *const cell[5], double *const face[3],
-                             double *dU[5], double *dB[3], orc_stats *st) {
+                             double *dU[5], double *dB[3], orc_stats *st, double *zout) {
   grid g;
   g.c = c;
+  g.st = st;
+  g.zout = zout;
   g.n[0] = c->nx; g.n[1] = c->ny; g.n[2] = c->nz;
   for (int d = 0; d < 3; ++d) {
     g.N[d] = g.n[d] + 2 * NG;
@@ -593,7 +696,19 @@ static size_t face_count(const orc_cfg *c, int d) {
 /* L(U): exported for the tests. */
 void orc_rhs(const orc_cfg *c, double *const cell[5], double *const face[3],
              double *dU[5], double *dB[3], orc_stats *st) {
-  spatial_operator(c, cell, face, dU, dB, st);
+  spatial_operator(c, cell, face, dU, dB, st, NULL);
+}
+
+/* ORC_LEARNED: the network's logit on every interior cell's lower face,
+ * logits[d * nx*ny*nz + s] (one operator evaluation, result discarded). */
+void orc_switch_logits(const orc_cfg *c, double *const cell[5], double *const face[3], double *logits) {
+  size_t nc = (size_t)c->nx * c->ny * c->nz;
+  double *du[5], *db[3];
+  for (int v = 0; v < 5; ++v) du[v] = malloc(nc * sizeof(double));
+  for (int d = 0; d < 3; ++d) db[d] = malloc(face_count(c, d) * sizeof(double));
+  spatial_operator(c, cell, face, du, db, NULL, logits);
+  for (int v = 0; v < 5; ++v) free(du[v]);
+  for (int d = 0; d < 3; ++d) free(db[d]);
 }
 
 /* One RK2 (Heun) step in place:
@@ -607,13 +722,13 @@ void orc_step(const orc_cfg *c, double *cell[5], double *face[3], double dt, orc
   for (int v = 0; v < 5; ++v) { us[v] = malloc(nc * sizeof(double)); du[v] = malloc(nc * sizeof(double)); }
   for (int d = 0; d < 3; ++d) { bs[d] = malloc(nfc[d] * sizeof(double)); db[d] = malloc(nfc[d] * sizeof(double)); }
 
-  spatial_operator(c, cell, face, du, db, st);
+  spatial_operator(c, cell, face, du, db, st, NULL);
   for (int v = 0; v < 5; ++v)
     for (size_t s = 0; s < nc; ++s) us[v][s] = cell[v][s] + dt * du[v][s];
   for (int d = 0; d < 3; ++d)
     for (size_t s = 0; s < nfc[d]; ++s) bs[d][s] = face[d][s] + dt * db[d][s];
 
-  spatial_operator(c, us, bs, du, db, st);
+  spatial_operator(c, us, bs, du, db, st, NULL);
   for (int v = 0; v < 5; ++v)
     for (size_t s = 0; s < nc; ++s) cell[v][s] = 0.5 * (cell[v][s] + us[v][s] + dt * du[v][s]);
   for (int d = 0; d < 3; ++d)
