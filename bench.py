@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="turbulence256",
-                   choices=["turbulence256", "ot2d128", "ot3d512", "blast_batch64"])
+                   choices=["turbulence256", "turbulence256_learned", "ot2d128", "ot3d512", "blast_batch64"])
     p.add_argument("--precision", default=None, choices=["mixed", "fp64", "fp32"])
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--tile", default="0,0,0")
@@ -165,6 +165,7 @@ def cpu_oracle_rate(seconds: float, n: int = 64):
 
 WORKLOADS = {
     "turbulence256": ("mixed", 256),
+    "turbulence256_learned": ("mixed", 256),
     "ot2d128": ("fp64", 128),
     "ot3d512": ("mixed", 512),
     "blast_batch64": ("fp32", 64),
@@ -190,6 +191,9 @@ def workload_config(args):
     text = {
         "turbulence256": f"turbulence_3d_{args.n}: 3D decaying MHD turbulence {args.n}^3 periodic, "
                          f"rho=1 p=0.6 rms Mach 1 beta=1, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
+        "turbulence256_learned": f"turbulence_3d_{args.n}_learned: 3D decaying MHD turbulence {args.n}^3 periodic "
+                                 f"as turbulence256, per-face learned HLL/HLLD switch (BF16 MLP 16-32-32-1, "
+                                 f"FP32 accumulation) trained on the GPU on 1e7 faces of FP64 runs (seed 5)",
         "ot2d128": f"orszag_tang_2d_{args.n}: 2D Orszag-Tang {args.n}^2 periodic, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
         "ot3d512": f"orszag_tang_3d_{args.n}: 3D Orszag-Tang {args.n}^3 periodic (+1% velocity noise), "
                    f"PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
@@ -241,8 +245,18 @@ def run_ours(args):
 
     tile = tuple(int(x) for x in args.tile.split(","))
     box = make_box(args)
+    learned = args.workload == "turbulence256_learned"
+    switch_rep = None
+    if learned:
+        # training (not timed): faces of FP64 turbulence runs with seed 5,
+        # the library's BF16 forward/backward and Adam kernels
+        from paper_2606_12753_gb300 import switch_train as T
+        sw, tau, switch_rep = T.train_switch(n=args.n, nfaces=10_000_000, seed=5, steps=3000, batch=16384)
     stream = torch.cuda.Stream()
-    solver = mhd.Solver(box, precision=args.precision, tile=tile, stream=stream.cuda_stream)
+    solver = mhd.Solver(box, precision=args.precision, riemann="learned" if learned else "hlld", tile=tile,
+                        stream=stream.cuda_stream)
+    if learned:
+        solver.set_switch(sw.block.data_ptr(), tau)
     solver.set_state(box.cell, box.face)
 
     def barrier():
@@ -252,7 +266,7 @@ def run_ours(args):
             torch.cuda.synchronize()
 
     solver.step_async(-1.0, args.warmup)
-    solver.stats()
+    st_w = solver.stats()
     solver.set_profiling(True)
     solver.profile()
     barrier()
@@ -281,7 +295,7 @@ def run_ours(args):
     per_launch_ms = stage_ms[k] / max(launches[k], 1)
     alg_bytes = STAGE_BYTES[args.precision][k] * box.ncell
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    tag = f"stage_kernel<{args.precision},{k + 1}>@{box.name}"
+    tag = f"stage_kernel{'_learned' if learned else ''}<{args.precision},{k + 1}>@{box.name}"
     traffic, src = traffic_from_profiles(tag)
     elem = 4 if args.precision == "fp32" else 8
     kelem = 8 if args.precision == "fp64" else 4
@@ -303,6 +317,10 @@ def run_ours(args):
         "stage_ms_per_launch": [stage_ms[0] / max(launches[0], 1), stage_ms[1] / max(launches[1], 1)],
         "gpu_launches": 2 * args.steps,
     }
+    if learned:
+        nh = st["faces_hll"] - st_w["faces_hll"]
+        nd = st["faces_hlld"] - st_w["faces_hlld"]
+        out["switch"] = {**switch_rep, "timed_hll_frac": nh / max(nh + nd, 1)}
     with_extras = rank == 0 and world == 1 and not args.no_extras
     if with_extras:
         # end to end through the public API with host buffers: per step the
@@ -356,6 +374,38 @@ def run_ours(args):
         cmp = {"fp64_value": box.ncell / (fp64_ms / 1e3) / 1e6, "unit": UNIT, "fp64_ms_per_step": fp64_ms,
                "steps": args.compare_steps, "dt": dt, "l1_rel_vs_fp64": l1,
                "note": "FP64 GPU path (parity with the FP64 oracle at 1e-12) as the reference"}
+        if learned:
+            # the method without the switch (HLLD on every face) and HLL on
+            # every face, same precision, same dt, same steps
+            for name in ("hlld", "hll"):
+                alt = mhd.Solver(box, precision=args.precision, riemann=name, stream=stream.cuda_stream)
+                alt.set_state(box.cell, box.face)
+                alt.step(dt, 1)
+                alt.set_state(box.cell, box.face)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                alt.step_async(dt, args.compare_steps)
+                e1.record(stream)
+                stream.synchronize()
+                ams = e0.elapsed_time(e1) / args.compare_steps
+                ac, af = alt.get_state()
+                alt.close()
+                al1 = {}
+                for v in range(5):
+                    al1[names[v]] = float(np.abs(ac[v] - rc[v]).sum() / np.abs(rc[v]).sum())
+                for d in range(3):
+                    al1[names[5 + d]] = float(np.abs(af[d] - rf[d]).sum() / max(np.abs(rf[d]).sum(), 1e-3 * bnorm))
+                cmp[f"{name}_ms_per_step"] = ams
+                cmp[f"{name}_l1_rel_vs_fp64"] = al1
+            solver.set_state(box.cell, box.face)
+            solver.step(dt, 1)
+            solver.set_state(box.cell, box.face)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            solver.step_async(dt, args.compare_steps)
+            e1.record(stream)
+            stream.synchronize()
+            cmp["learned_ms_per_step"] = e0.elapsed_time(e1) / args.compare_steps
         out["vs_fp64"] = cmp
         out["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
     elif rank == 0:

@@ -90,8 +90,9 @@ typedef struct {
 typedef struct {
   long long rho_floor_hits; /* cell-stage evaluations that hit the density floor */
   long long p_floor_hits;   /* ... the pressure floor */
-  long long faces_hll;      /* faces solved with HLL (MHD_LEARNED / MHD_HLL) */
-  long long faces_hlld;     /* faces solved with HLLD */
+  long long faces_hll;      /* MHD_LEARNED only: face solves (halo faces of neighbouring tiles
+                               recomputed included) that took HLL ... */
+  long long faces_hlld;     /* ... and that took HLLD */
   double last_dt;           /* dt of the last step taken */
   int status;               /* device status word (bit 0 non-finite, bit 1 timeout) */
   int steps;                /* steps taken since creation */
@@ -218,8 +219,22 @@ int mhd_dump_faces(mhd_handle* h, const long long* face_ids, long long n, float*
                    float* scores);
 /* Use the network in `block` (device, copied) to choose the solver of every
  * face when the handle's riemann is MHD_LEARNED: HLLD when sigmoid(logit) >=
- * tau, HLL otherwise. */
+ * tau (a logit that is not finite also takes HLLD), HLL otherwise.  The
+ * features and the network run in the handle's precision up to the bf16
+ * inputs and FP32 accumulation of the tensor cores.  Stepping (mhd_step,
+ * mhd_rhs, ...) a MHD_LEARNED handle before this call fails with
+ * MHD_ERR_INVALID.  The switch is instantiated for the 16x8 tile (the
+ * default); tau must lie in (0, 1).  Synchronises. */
 int mhd_set_switch(mhd_handle* h, const void* block, double tau);
+
+/* The switch's choice on every face of the current state, from the stage
+ * kernel itself: choices[d * nx*ny*nz + s] = 1 when the lower face of cell s
+ * along axis d takes HLLD, 0 when it takes HLL; logits (may be NULL) receives
+ * the network's logit there.  Both are device arrays of 3 * nx*ny*nz
+ * elements, caller-owned; the top face of an outflow axis is not reported
+ * (left untouched).  The handle's riemann must be MHD_LEARNED with a network
+ * set.  The state is unchanged; synchronises. */
+int mhd_switch_choices(mhd_handle* h, unsigned char* choices, float* logits);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent boxes of uneven size advanced together in ONE

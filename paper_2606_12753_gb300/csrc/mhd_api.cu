@@ -1,5 +1,6 @@
 // C ABI of the MHD hot path: handle, device buffers, launches, reductions.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -22,12 +23,27 @@ cudaError_t set_smem_fp32(int, int, size_t);
 size_t smem_bytes_fp64(int, int);
 size_t smem_bytes_mixed(int, int);
 size_t smem_bytes_fp32(int, int);
+cudaError_t launch_stage_learned_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_learned_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_learned_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t set_smem_learned_fp64(size_t);
+cudaError_t set_smem_learned_mixed(size_t);
+cudaError_t set_smem_learned_fp32(size_t);
 cudaError_t launch_prims_fp64(unsigned, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_prims_mixed(unsigned, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_prims_fp32(unsigned, cudaStream_t, const Geo&, const StageArgs&);
 
 cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nb, size_t smem, cudaStream_t st,
                          const Geo& g, const StageArgs& a) {
+  if (g.riemann == 2) {
+    // learned switch: needs the network; 16 x 8 tile only
+    if (!a.mlp) return cudaErrorInvalidValue;
+    switch (prec) {
+      case P_FP64: return launch_stage_learned_fp64(stage, nb, smem, st, g, a);
+      case P_MIXED: return launch_stage_learned_mixed(stage, nb, smem, st, g, a);
+      default: return launch_stage_learned_fp32(stage, nb, smem, st, g, a);
+    }
+  }
   switch (prec) {
     case P_FP64: return launch_stage_fp64(stage, tx, ty, nb, smem, st, g, a);
     case P_MIXED: return launch_stage_mixed(stage, tx, ty, nb, smem, st, g, a);
@@ -39,6 +55,13 @@ cudaError_t launch_prims(int prec, unsigned nb, cudaStream_t st, const Geo& g, c
     case P_FP64: return launch_prims_fp64(nb, st, g, a);
     case P_MIXED: return launch_prims_mixed(nb, st, g, a);
     default: return launch_prims_fp32(nb, st, g, a);
+  }
+}
+cudaError_t stage_set_smem_learned(int prec, size_t bytes) {
+  switch (prec) {
+    case P_FP64: return set_smem_learned_fp64(bytes);
+    case P_MIXED: return set_smem_learned_mixed(bytes);
+    default: return set_smem_learned_fp32(bytes);
   }
 }
 cudaError_t stage_set_smem(int prec, int tx, int ty, size_t bytes) {
@@ -84,7 +107,7 @@ struct mhd_handle {
   int steps = 0;
   bool profiling = false;
   void* mlp = nullptr;                     // copy of the switch network (device)
-  float mlp_tau = 0.5f;
+  float mlp_zt = 0.0f;                     // logit of the switch threshold tau
   std::vector<cudaEvent_t> ev_pool;        // 3 events per recorded step
   size_t ev_used = 0;
   std::string err;
@@ -161,6 +184,8 @@ static int validate(const mhd_config* c, mhd_handle* h) {
   if (tz < 1 || tz > (1 << 20)) return fail(h, MHD_ERR_INVALID, "tile_z out of range");
   if (!stage_tile_supported(c->precision, tx, ty))
     return fail(h, MHD_ERR_INVALID, "tile %dx%d is not instantiated for this precision", tx, ty);
+  if (c->riemann == MHD_LEARNED && (tx != 16 || ty != 8))
+    return fail(h, MHD_ERR_INVALID, "the learned switch is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
   if (stage_smem_bytes(c->precision, tx, ty) > 227 * 1024)
     return fail(h, MHD_ERR_INVALID, "tile %dx%d needs %zu B of shared memory (> 227 KB)", tx, ty,
                 stage_smem_bytes(c->precision, tx, ty));
@@ -239,6 +264,7 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   if (e == cudaSuccess) e = cudaMemsetAsync(h->U[0], 0, bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->K1, 0, kbytes, h->stream);
   if (e == cudaSuccess) e = stage_set_smem(cfg->precision, h->geo.TX, h->geo.TY, h->smem_bytes);
+  if (e == cudaSuccess && cfg->riemann == MHD_LEARNED) e = stage_set_smem_learned(cfg->precision, h->smem_bytes);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     fail(nullptr, MHD_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
@@ -319,7 +345,7 @@ static StageArgs base_args(mhd_handle* h) {
   a.status = h->status;
   a.counters = h->counters;
   a.mlp = (const float*)h->mlp;
-  a.mlp_tau = h->mlp_tau;
+  a.mlp_zt = h->mlp_zt;
   return a;
 }
 
@@ -377,7 +403,14 @@ static cudaError_t launch_step(mhd_handle* h, double dt) {
   return cudaSuccess;
 }
 
+static int need_switch(mhd_handle* h) {
+  if (h->cfg.riemann == MHD_LEARNED && !h->mlp)
+    return fail(h, MHD_ERR_INVALID, "riemann is MHD_LEARNED but no network was set (mhd_set_switch)");
+  return MHD_OK;
+}
+
 static int enqueue_steps(mhd_handle* h, double dt, int nsteps) {
+  if (int rc = need_switch(h)) return rc;
   for (int s = 0; s < nsteps; ++s) {
     cudaError_t e = launch_step(h, dt);
     if (e != cudaSuccess) return fail(h, MHD_ERR_CUDA, "stage launch failed: %s", cudaGetErrorString(e));
@@ -434,6 +467,7 @@ extern "C" int mhd_step(mhd_handle* h, double dt, int nsteps) {
 
 extern "C" int mhd_rhs(mhd_handle* h, void* cell[5], void* face[3], int on_device) {
   if (!h) return MHD_ERR_INVALID;
+  if (int rc = need_switch(h)) return rc;
   cudaError_t e = ensure_prims(h);
   if (e) return fail(h, MHD_ERR_CUDA, "primitive recovery failed: %s", cudaGetErrorString(e));
   const Geo& g = h->geo;
@@ -741,6 +775,8 @@ extern "C" int mhd_batch_create(int nbox, const mhd_config* cfgs, void* cuda_str
     if (rc) return bfail(nullptr, rc, "box %d: %s", i, g_create_err.c_str());
     if (cfgs[i].precision != cfgs[0].precision || cfgs[i].riemann != cfgs[0].riemann || cfgs[i].emf != cfgs[0].emf)
       return bfail(nullptr, MHD_ERR_INVALID, "all boxes of a batch share precision, Riemann solver and EMF mode");
+    if (cfgs[i].riemann == MHD_LEARNED)
+      return bfail(nullptr, MHD_ERR_INVALID, "batches solve with HLLD or HLL; the learned switch is single-box only");
   }
   mhd_batch* b = new (std::nothrow) mhd_batch();
   if (!b) return bfail(nullptr, MHD_ERR_NOMEM, "host allocation failed");
@@ -1180,6 +1216,30 @@ extern "C" int mhd_set_switch(mhd_handle* h, const void* block, double tau) {
   if (!h->mlp) CUDA_TRY(h, cudaMalloc(&h->mlp, mlp_param_bytes()));
   CUDA_TRY(h, cudaMemcpyAsync(h->mlp, block, mlp_param_bytes(), cudaMemcpyDeviceToDevice, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  h->mlp_tau = (float)tau;
+  h->mlp_zt = (float)log(tau / (1.0 - tau));
   return MHD_OK;
+}
+
+extern "C" int mhd_switch_choices(mhd_handle* h, unsigned char* choices, float* logits) {
+  if (!h) return MHD_ERR_INVALID;
+  if (h->cfg.riemann != MHD_LEARNED) return fail(h, MHD_ERR_INVALID, "the handle's riemann is not MHD_LEARNED");
+  if (!choices) return fail(h, MHD_ERR_INVALID, "null choices pointer");
+  if (int rc = need_switch(h)) return rc;
+  cudaError_t e = ensure_prims(h);
+  if (e) return fail(h, MHD_ERR_CUDA, "primitive recovery failed: %s", cudaGetErrorString(e));
+  const Geo& g = h->geo;
+  StageArgs a = base_args(h);
+  a.dt = 1.0;
+  a.dtword = h->words + h->parity;
+  a.nextword = h->words + 4;
+  a.U = h->U[h->cur];
+  a.Win = h->W[h->cur];
+  a.K1out = h->K1;                          // scratch: the operator's value is discarded
+  a.Wout = nullptr;
+  a.choices = choices;
+  a.logits = logits;
+  e = launch_stage(h->cfg.precision, 1, g.TX, g.TY, (unsigned)(g.ntx * g.nty * g.nchunk), h->smem_bytes,
+                   h->stream, g, a);
+  if (e) return fail(h, MHD_ERR_CUDA, "stage launch failed: %s", cudaGetErrorString(e));
+  return check_status(h);
 }

@@ -71,33 +71,28 @@ __host__ __device__ __forceinline__ void face_features(const R* wl, const R* wr,
   f[15] = (float)(rmin(cl, cr) * ic);
 }
 
-// Warp-level forward pass for 32 faces whose features (bf16, row-major
-// [32][16]) are in shared memory F.  Returns in every lane the logit of
-// face `lane`.  wb: bf16 weights, bias: master block (b1, b2, b3 read from
-// it).  All 32 lanes must call it.
-__device__ __forceinline__ float mlp_forward_warp(const uint16_t* F, const uint16_t* wb, const float* master,
-                                                  float* h1_out = nullptr, float* h2_out = nullptr) {
+// Warp-level forward pass from the A fragments of the two 16-row tiles of
+// the bf16 feature matrix (rows = faces 0..31 of the warp).  Returns in
+// every lane the logit of face `lane`.  wb: bf16 weights, master: the FP32
+// block (b1, b2, b3 read from it).  All 32 lanes must call it.
+__device__ __forceinline__ float mlp_forward_frags(const uint32_t (&a1)[2][4], const uint16_t* wb,
+                                                   const float* master, float* h1_out = nullptr,
+                                                   float* h2_out = nullptr) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
-  const uint32_t* F32 = reinterpret_cast<const uint32_t*>(F);
   const uint32_t* W = reinterpret_cast<const uint32_t*>(wb);
-  float zres[2][2];
+  float z0lo = 0.f, z0hi = 0.f, z1lo = 0.f, z1hi = 0.f;
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt) {
+    const uint32_t* af = a1[mt];
     // layer 1: [16 x 16] x W1^T [16 x 32]
-    uint32_t a[4];
-    const int r0 = mt * 16 + g, r1 = r0 + 8;
-    a[0] = F32[(r0 * 16 + 2 * t) >> 1];
-    a[1] = F32[(r1 * 16 + 2 * t) >> 1];
-    a[2] = F32[(r0 * 16 + 2 * t + 8) >> 1];
-    a[3] = F32[(r1 * 16 + 2 * t + 8) >> 1];
     float h1[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       const int n = nt * 8 + g;
       const float b0 = master[MLP_OFF_B1 + nt * 8 + 2 * t], b1 = master[MLP_OFF_B1 + nt * 8 + 2 * t + 1];
       h1[nt][0] = b0; h1[nt][1] = b1; h1[nt][2] = b0; h1[nt][3] = b1;
-      mma_16816(h1[nt], a, W[(MLP_WB_W1 + n * 16 + 2 * t) >> 1], W[(MLP_WB_W1 + n * 16 + 2 * t + 8) >> 1]);
+      mma_16816(h1[nt], af, W[(MLP_WB_W1 + n * 16 + 2 * t) >> 1], W[(MLP_WB_W1 + n * 16 + 2 * t + 8) >> 1]);
     }
     // layer 2: [16 x 32] x W2^T [32 x 32]
     uint32_t a2[2][4];
@@ -146,18 +141,69 @@ __device__ __forceinline__ float mlp_forward_warp(const uint16_t* F, const uint1
       const uint32_t bb1 = g == 0 ? W[(MLP_WB_W3 + ks * 16 + 2 * t + 8) >> 1] : 0u;
       mma_16816(z, a3, bb0, bb1);
     }
-    zres[mt][0] = z[0];   // face mt*16 + g, valid in lanes with t == 0
-    zres[mt][1] = z[2];   // face mt*16 + g + 8
+    // face mt*16 + g in z[0], face mt*16 + g + 8 in z[2] (lanes with t == 0)
+    if (mt == 0) { z0lo = z[0]; z0hi = z[2]; }
+    else { z1lo = z[0]; z1hi = z[2]; }
   }
   // bring the logit of face `lane` to lane `lane`
   const int mt = lane >> 4, r = lane & 15;
   const int src = (r & 7) * 4;
-  const float v00 = __shfl_sync(0xffffffffu, zres[0][0], src);
-  const float v01 = __shfl_sync(0xffffffffu, zres[0][1], src);
-  const float v10 = __shfl_sync(0xffffffffu, zres[1][0], src);
-  const float v11 = __shfl_sync(0xffffffffu, zres[1][1], src);
+  const float v00 = __shfl_sync(0xffffffffu, z0lo, src);
+  const float v01 = __shfl_sync(0xffffffffu, z0hi, src);
+  const float v10 = __shfl_sync(0xffffffffu, z1lo, src);
+  const float v11 = __shfl_sync(0xffffffffu, z1hi, src);
   const float lo = mt == 0 ? v00 : v10, hi = mt == 0 ? v01 : v11;
   return r < 8 ? lo : hi;
+}
+
+// Forward pass for 32 faces whose features (bf16, row-major [32][16]) are in
+// shared memory F.
+__device__ __forceinline__ float mlp_forward_warp(const uint16_t* F, const uint16_t* wb, const float* master,
+                                                  float* h1_out = nullptr, float* h2_out = nullptr) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const uint32_t* F32 = reinterpret_cast<const uint32_t*>(F);
+  uint32_t a[2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+    a[mt][0] = F32[(r0 * 16 + 2 * t) >> 1];
+    a[mt][1] = F32[(r1 * 16 + 2 * t) >> 1];
+    a[mt][2] = F32[(r0 * 16 + 2 * t + 8) >> 1];
+    a[mt][3] = F32[(r1 * 16 + 2 * t + 8) >> 1];
+  }
+  return mlp_forward_frags(a, wb, master, h1_out, h2_out);
+}
+
+// Forward pass for 32 faces whose features each lane holds in registers
+// (f: the 16 features of face `lane`).  The A fragments are assembled with
+// warp shuffles: lane (g, t) of row tile mt needs feature pairs t and t+4 of
+// faces mt*16+g and mt*16+g+8.
+__device__ __forceinline__ float mlp_forward_regs(const float* f, const uint16_t* wb, const float* master) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t p[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) p[j] = pack_bf16x2(f[2 * j], f[2 * j + 1]);
+  uint32_t a[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t x0 = __shfl_sync(0xffffffffu, p[j], r0);
+      const uint32_t x1 = __shfl_sync(0xffffffffu, p[j], r1);
+      const uint32_t y0 = __shfl_sync(0xffffffffu, p[j + 4], r0);
+      const uint32_t y1 = __shfl_sync(0xffffffffu, p[j + 4], r1);
+      if (t == j) {
+        a[mt][0] = x0;
+        a[mt][1] = x1;
+        a[mt][2] = y0;
+        a[mt][3] = y1;
+      }
+    }
+  }
+  return mlp_forward_frags(a, wb, master);
 }
 
 }  // namespace mhd

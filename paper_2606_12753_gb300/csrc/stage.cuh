@@ -65,8 +65,10 @@ struct StageArgs {
   unsigned int* status;
   unsigned long long* counters;
   double dt;           // > 0: explicit; <= 0: cfl / *dtword
-  const float* mlp;    // learned-switch weights (packed), or null
-  float mlp_tau;
+  const float* mlp;    // learned-switch parameter block (FP32 masters, then bf16 weights), or null
+  float mlp_zt;        // logit threshold: HLLD when logit >= mlp_zt
+  unsigned char* choices;   // learned switch, stage 1: per owned face 1 = HLLD, 0 = HLL (or null)
+  float* logits;            // ... and the network's logit (or null)
 };
 
 __host__ __device__ inline int wrapc(int i, int n, int bc) {

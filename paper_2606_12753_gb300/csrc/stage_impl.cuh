@@ -17,6 +17,7 @@
 // US of the paper's MHD step (Sec. 2.2, Table 2) fused into one pass per
 // RK stage.
 #pragma once
+#include "mlp.cuh"
 #include "stage.cuh"
 
 namespace mhd {
@@ -46,8 +47,11 @@ struct Tile {
   static constexpr int nRtot = oDU + 2 * 5 * nC;
   // new face values (type S): NBX[nE], NBY[nE], NBZ[2][nC]
   static constexpr int nS = 2 * nE + 2 * nC;
-  // index tables (int): colc[W], rowc[H]
-  static constexpr int nI = W + H;
+  // index tables (int): colc[W], rowc[H], then the queue counters of the
+  // learned switch (HLL and HLLD items, one pair per plane parity)
+  static constexpr int nI = W + H + 4;
+  // flux items of one plane: z-faces, x-faces, y-faces
+  static constexpr int nItems = nZ + nX + nY;
   template <typename R, typename S>
   static constexpr size_t bytes() {
     size_t b = (size_t)nRtot * sizeof(R);
@@ -125,7 +129,7 @@ __device__ void cell_prims(const Geo& g, const StageArgs& a, double dt, int i, i
   recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], bxl, bxh, byl, byh, bzl, bzh, w, rho_hit, p_hit);
 }
 
-template <int PREC, int STAGE, int TX, int TY>
+template <int PREC, int STAGE, int TX, int TY, bool LEARN = false>
 struct StageKernel {
   using R = typename Prec<PREC>::R;
   using S = typename Prec<PREC>::S;
@@ -227,7 +231,12 @@ struct StageKernel {
         face<1>(g, sm, c, BNq[T::nR + r], sm + T::oHY, sm + T::oYC + (q & 1) * 3 * T::nY, T::nY, o);
       }
     }
-    // cell-centred E_c = -v x B_c of plane q
+    cell_emf(sm, q);
+  }
+
+  // cell-centred E_c = -v x B_c of plane q
+  static __device__ __forceinline__ void cell_emf(R* sm, int q) {
+    const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
     R* EC = sm + T::oEC + (q & 1) * 3 * T::nZ;
     for (int w = threadIdx.x; w < T::nZ; w += blockDim.x) {
       const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
@@ -238,6 +247,155 @@ struct StageKernel {
       EC[T::nZ + w] = vx * bz - vz * bx;
       EC[2 * T::nZ + w] = vy * bx - vx * by;
     }
+  }
+
+  // ------------------------------------------------- phase B, learned switch
+  // Stencil of flux item w of plane q (the z-faces k+1/2 first when nZ > 0,
+  // then the x- and y-faces of plane q): the four cells across the face in
+  // its rotated order and the normal field.  Returns the face's axis and its
+  // slot o in that axis' flux arrays.
+  static __device__ __forceinline__ int item_stencil(const R* sm, int k, int q, int nZ, int w, R (&c)[4][7], R& bn,
+                                                     int& o) {
+    const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
+    const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
+    if (w < nZ) {
+      const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
+      const int r = (i + 2) + W * (j + 2);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) gather<2>(sm + T::oP + ((k - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
+      bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
+      o = w;
+      return 2;
+    }
+    if (w < nZ + T::nX) {
+      o = w - nZ;
+      const int i = o % (TX + 1), j = o / (TX + 1) - 1;
+      const int r = (i + 2) + W * (j + 2);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) gather<0>(Pq, T::nR, r - 2 + s, c[s]);
+      bn = BNq[r];
+      return 0;
+    }
+    o = w - nZ - T::nX;
+    const int i = o % (TX + 2) - 1, j = o / (TX + 2);
+    const int r = (i + 2) + W * (j + 2);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) gather<1>(Pq, T::nR, r + (s - 2) * W, c[s]);
+    bn = BNq[T::nR + r];
+    return 1;
+  }
+
+  // Store the flux of slot o on axis D (same layout as face<D>).
+  template <int D>
+  static __device__ __forceinline__ void store_flux(const Geo& g, R* sm, int q, int o, const R* f, R cm, R rl, R rr) {
+    R* H;
+    R* C;
+    int n;
+    if (D == 2) { H = sm + T::oHZ; C = sm + T::oZC; n = T::nZ; }
+    else if (D == 0) { H = sm + T::oHX; C = sm + T::oXC + (q & 1) * 3 * T::nX; n = T::nX; }
+    else { H = sm + T::oHY; C = sm + T::oYC + (q & 1) * 3 * T::nY; n = T::nY; }
+    H[0 * n + o] = f[0];
+    H[(1 + D) * n + o] = f[1];
+    H[(1 + (D + 1) % 3) * n + o] = f[2];
+    H[(1 + (D + 2) % 3) * n + o] = f[3];
+    H[4 * n + o] = f[4];
+    C[o] = -f[5];
+    C[n + o] = f[6];
+    C[2 * n + o] = oriented_mass_flux(f[0], rl, rr, cm, (R)g.deadband);
+  }
+  static __device__ __forceinline__ void store_any(int D, const Geo& g, R* sm, int q, int o, const R* f, R cm, R rl,
+                                                   R rr) {
+    if (D == 0) store_flux<0>(g, sm, q, o, f, cm, rl, rr);
+    else if (D == 1) store_flux<1>(g, sm, q, o, f, cm, rl, rr);
+    else store_flux<2>(g, sm, q, o, f, cm, rl, rr);
+  }
+
+  // Cell (relative to the tile origin) whose lower face along D is flux
+  // slot o.
+  static __device__ __forceinline__ void slot_cell(int D, int o, int& i, int& j) {
+    if (D == 2) { i = o % (TX + 2) - 1; j = o / (TX + 2) - 1; }
+    else if (D == 0) { i = o % (TX + 1); j = o / (TX + 1) - 1; }
+    else { i = o % (TX + 2) - 1; j = o / (TX + 2); }
+  }
+
+  // Flux phase with the learned switch.  Pass 1, one warp per 32 faces: PLM
+  // reconstruction, the 16 features and the network on the tensor cores
+  // classify each face; its item index goes to the front of a shared-memory
+  // queue when HLL suffices, to the back when HLLD is needed (a non-finite
+  // logit counts as "needed").  Pass 2 solves the queue densely -- HLL items
+  // first, then HLLD -- so neither solver diverges against the other.
+  static __device__ void fluxes_learned(const Geo& g, const StageArgs& a, R* sm, unsigned short* queue, int* qcnt,
+                                        int k, int q, bool with_z, int gi0, int gj0, int kb, int ke, unsigned& nh,
+                                        unsigned& nd) {
+    const int nZ = with_z ? T::nZ : 0;
+    const int nitems = nZ + T::nX + T::nY;
+    const int lane = threadIdx.x & 31;
+    const R gam = (R)g.gamma;
+    const float* master = a.mlp;
+    const uint16_t* wb =
+        reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(a.mlp) + MLP_MASTER_BYTES);
+    int* cnt = qcnt + 2 * (q & 1);   // [0] HLL items (front), [1] HLLD items (back)
+    const bool record = a.choices != nullptr && q >= kb && q < ke;
+    for (int base = threadIdx.x & ~31; base < nitems; base += blockDim.x) {
+      const int w = base + lane;
+      const bool valid = w < nitems;
+      int o = 0, D = 0;
+      float feat[MLP_NF];
+      if (valid) {
+        R c[4][7], wl[7], wr[7], bn;
+        D = item_stencil(sm, k, q, nZ, w, c, bn, o);
+        plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+        face_features<R>(wl, wr, bn, fast_speed(wl, bn, gam), fast_speed(wr, bn, gam), feat);
+      } else {
+#pragma unroll
+        for (int v = 0; v < MLP_NF; ++v) feat[v] = 0.f;
+      }
+      const float z = mlp_forward_regs(feat, wb, master);
+      const bool need = !(z < a.mlp_zt);
+      const unsigned bd = __ballot_sync(0xffffffffu, valid && need);
+      const unsigned bh = __ballot_sync(0xffffffffu, valid && !need);
+      int ph = 0, pd = 0;
+      if (lane == 0) {
+        if (bh) ph = atomicAdd(&cnt[0], __popc(bh));
+        if (bd) pd = atomicAdd(&cnt[1], __popc(bd));
+      }
+      ph = __shfl_sync(0xffffffffu, ph, 0);
+      pd = __shfl_sync(0xffffffffu, pd, 0);
+      const unsigned below = (1u << lane) - 1u;
+      if (valid) {
+        if (need) queue[nitems - 1 - (pd + __popc(bd & below))] = (unsigned short)w;
+        else queue[ph + __popc(bh & below)] = (unsigned short)w;
+      }
+      if (record && valid) {
+        int i, j;
+        slot_cell(D, o, i, j);
+        const int gi = gi0 + i, gj = gj0 + j;
+        if (i >= 0 && i < TX && j >= 0 && j < TY && gi < g.n[0] && gj < g.n[1]) {
+          const long long s = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * q);
+          a.choices[D * g.ncell + s] = need ? 1 : 0;
+          if (a.logits) a.logits[D * g.ncell + s] = z;
+        }
+      }
+    }
+    __syncthreads();
+    const int nhll = cnt[0];
+    if (threadIdx.x < 2) qcnt[2 * ((q + 1) & 1) + threadIdx.x] = 0;   // next plane's counters; read before a barrier
+    for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
+      const int w = queue[t];
+      R c[4][7], wl[7], wr[7], f[7], bn, cm;
+      int o;
+      const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
+      plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+      if (t < nhll) {
+        hll_flux(wl, wr, bn, gam, f, &cm);
+        ++nh;
+      } else {
+        hlld_flux(wl, wr, bn, gam, f, &cm);
+        ++nd;
+      }
+      store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
+    }
+    cell_emf(sm, q);
   }
 
   // ---------------------------------------------------------------- phase C
@@ -434,6 +592,11 @@ struct StageKernel {
     constexpr size_t iOff = ((sOff + (size_t)T::nS * sizeof(S)) + 15) / 16 * 16;
     int* colc = reinterpret_cast<int*>(smem_raw + iOff);
     int* rowc = colc + W;
+    int* qcnt = rowc + T::H;
+    // the HLLD queue of the learned switch lives in the new-face buffer,
+    // which is idle from the start of the flux phase to new_faces
+    unsigned short* queue = reinterpret_cast<unsigned short*>(NB);
+    static_assert((size_t)T::nItems * sizeof(unsigned short) <= (size_t)T::nS * sizeof(S), "queue does not fit");
 
     int b = item;
     const int tile_x = b % g.ntx;
@@ -455,9 +618,10 @@ struct StageKernel {
       if (t < T::W) colc[t] = wrapc(gi0 - 2 + t, g.n[0], g.bc[0]);
       else rowc[t - T::W] = wrapc(gj0 - 2 + (t - T::W), g.n[1], g.bc[1]);
     }
+    if (LEARN && threadIdx.x < 4) qcnt[threadIdx.x] = 0;
     __syncthreads();
 
-    unsigned nrho = 0, np = 0;
+    unsigned nrho = 0, np = 0, nh = 0, nd = 0;
     bool bad = false;
     R smax = R(0);
 
@@ -465,12 +629,14 @@ struct StageKernel {
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 1, true);
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb, true);
     __syncthreads();
-    fluxes(g, sm, kb - 2, kb - 1, false);
+    if (LEARN) fluxes_learned(g, a, sm, queue, qcnt, kb - 2, kb - 1, false, gi0, gj0, kb, ke, nh, nd);
+    else fluxes(g, sm, kb - 2, kb - 1, false);
     __syncthreads();
     for (int k = kb - 1; k < ke; ++k) {
       load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true);
       __syncthreads();
-      fluxes(g, sm, k, k + 1, true);
+      if (LEARN) fluxes_learned(g, a, sm, queue, qcnt, k, k + 1, true, gi0, gj0, kb, ke, nh, nd);
+      else fluxes(g, sm, k, k + 1, true);
       __syncthreads();
       divergence_and_edges(g, sm, k);
       __syncthreads();
@@ -488,6 +654,14 @@ struct StageKernel {
     double sm64 = (double)smax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sm64 = fmax(sm64, __shfl_xor_sync(mask, sm64, o));
+    if (LEARN) {
+      nh = __reduce_add_sync(mask, nh);
+      nd = __reduce_add_sync(mask, nd);
+      if ((threadIdx.x & 31) == 0) {
+        if (nh) atomicAdd(&a.counters[C_HLL], (unsigned long long)nh);
+        if (nd) atomicAdd(&a.counters[C_HLLD], (unsigned long long)nd);
+      }
+    }
     if ((threadIdx.x & 31) == 0) {
       if (nrho) atomicAdd(&a.counters[C_RHO_FLOOR], (unsigned long long)nrho);
       if (np) atomicAdd(&a.counters[C_P_FLOOR], (unsigned long long)np);
@@ -501,6 +675,13 @@ template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256) stage_kernel(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY>::run_item(g, a, blockIdx.x, smem_raw);
+}
+
+// The same stage with the learned HLL/HLLD face switch.
+template <int PREC, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_learned(Geo g, StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageKernel<PREC, STAGE, TX, TY, true>::run_item(g, a, blockIdx.x, smem_raw);
 }
 
 // Primitives (and the CFL max) of a state set from outside: one thread per cell.

@@ -48,4 +48,22 @@ cudaError_t launch_prims_mixed(unsigned nblocks, cudaStream_t st, const Geo& g, 
   return cudaGetLastError();
 }
 
+// The learned HLL/HLLD switch is instantiated for the 16 x 8 tile only.
+cudaError_t launch_stage_learned_mixed(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
+                                   const StageArgs& args) {
+  if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
+  if (stage == 1) stage_kernel_learned<P_MIXED, 1, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  else stage_kernel_learned<P_MIXED, 2, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  return cudaGetLastError();
+}
+
+cudaError_t set_smem_learned_mixed(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel_learned<P_MIXED, 1, 16, 8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage_kernel_learned<P_MIXED, 2, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  return e;
+}
+
 }  // namespace mhd

@@ -59,7 +59,7 @@ EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state",
            "mhd_batch_set_barrier_timeout", "mhd_batch_inject_missed_arrival", "mhd_batch_box_dt",
            "mhd_batch_get_stats", "mhd_batch_destroy", "mhd_batch_last_error",
            "mlp_param_bytes", "mlp_init", "mlp_forward", "mlp_backward", "mlp_adam", "mhd_dump_faces",
-           "mhd_set_switch"]
+           "mhd_set_switch", "mhd_switch_choices"]
 
 _lib = None
 
@@ -147,6 +147,8 @@ def load(build: bool = True):
     L.mhd_dump_faces.argtypes = [_H, _VP, C.c_longlong, _VP, _VP, _VP]
     L.mhd_set_switch.restype = C.c_int
     L.mhd_set_switch.argtypes = [_H, _VP, C.c_double]
+    L.mhd_switch_choices.restype = C.c_int
+    L.mhd_switch_choices.argtypes = [_H, _VP, _VP]
     L.mhd_last_error.restype = C.c_char_p
     L.mhd_last_error.argtypes = [_H]
     _lib = L
@@ -327,6 +329,14 @@ class Solver:
     def stats(self) -> dict:
         return mhd_get_stats(self.h)
 
+    def set_switch(self, block_ptr, tau: float):
+        """Network (device parameter block, copied) and threshold of the learned switch."""
+        mhd_set_switch(self.h, block_ptr, tau)
+
+    def switch_choices(self, choices_ptr, logits_ptr=None):
+        """Per-face choices (device uint8[3 * ncell], 1 = HLLD) and logits of the current state."""
+        mhd_switch_choices(self.h, choices_ptr, logits_ptr)
+
     def close(self):
         if self.h:
             mhd_destroy(self.h)
@@ -484,3 +494,7 @@ def mhd_dump_faces(h, ids_ptr, n, x_ptr, y_ptr, score_ptr=None):
 
 def mhd_set_switch(h, block_ptr, tau):
     _check(h, load().mhd_set_switch(h, _VP(block_ptr), tau))
+
+
+def mhd_switch_choices(h, choices_ptr, logits_ptr=None):
+    _check(h, load().mhd_switch_choices(h, _VP(choices_ptr), _VP(logits_ptr or 0)))

@@ -66,3 +66,21 @@ def test_tile_smem_limit():
     with pytest.raises(mhd.MHDError) as ei:
         mhd.mhd_create(c)
     assert "instantiated" in str(ei.value) or "shared memory" in str(ei.value)
+
+
+def test_learned_switch_needs_the_16x8_tile():
+    c = mhd.mhd_default_config(32, 32, 32)
+    c.riemann = mhd.MHD_LEARNED
+    c.precision = mhd.MHD_MIXED
+    c.tile_x, c.tile_y = 8, 8
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert "16x8" in str(ei.value)
+
+
+def test_batch_rejects_the_learned_switch():
+    from paper_2606_12753_gb300 import inputs as I
+    boxes = [I.uniform_state((16, 16, 16)), I.uniform_state((8, 16, 16))]
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.Batch(boxes, precision="fp32", riemann="learned")
+    assert "learned" in str(ei.value)

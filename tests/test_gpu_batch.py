@@ -48,10 +48,29 @@ def test_batch_fp64_matches_oracle_with_per_box_cfl_dt():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_batch_matches_oracle_with_explicit_dt(precision):
+    """The FP32 and mixed batch against the FP64 oracle on the same dt
+    sequence, at the FP32 parity tolerance."""
+    boxes = small_blasts(5, seed=6)
+    dt = min(O.cfl_dt(ocfg(bx), bx.cell, bx.face) for bx in boxes)
+    b = load_batch(boxes, precision)
+    b.step(dt, 3)
+    worst = {}
+    for i, bx in enumerate(boxes):
+        rc, rf = O.step_dts(ocfg(bx), bx.cell, bx.face, [dt] * 3)
+        c, f = b.get_state(i)
+        errs = state_errors(c, f, rc, rf)
+        worst[bx.name] = max(errs.values())
+    b.close()
+    assert max(worst.values()) <= 1e-5, worst
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
 def test_batch_matches_single_box_path(precision):
     """Same method, different kernels (the persistent kernel inlines the stage
-    body, so FMA contraction may differ): agreement at the FP32 parity
-    tolerance (low-beta blasts amplify FP32 rounding in the pressure)."""
+    body, so FMA contraction may differ).  Each is held to the oracle at the
+    FP32 parity tolerance 1e-5 elsewhere, so their difference is bounded by
+    twice that (low-beta blasts amplify FP32 rounding in the pressure)."""
     from paper_2606_12753_gb300 import mhd
     boxes = small_blasts(5, seed=6)
     b = load_batch(boxes, precision)
@@ -64,7 +83,7 @@ def test_batch_matches_single_box_path(precision):
         s.close()
         c, f = b.get_state(i)
         errs = state_errors(c, f, rc, rf)
-        assert max(errs.values()) <= 1e-5, (i, errs)
+        assert max(errs.values()) <= 2e-5, (i, errs)
     b.close()
 
 
