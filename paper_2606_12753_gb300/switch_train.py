@@ -1,10 +1,10 @@
 """Training of the learned HLL/HLLD face switch on the GPU.
 
-The data are faces the method itself produces: FP64 runs of a periodic box
-(HLLD everywhere) are paused at a few snapshots, and at each a seeded random
-set of faces is sampled with ``mhd_dump_faces`` -- 16 features of the
-reconstructed states, and the label 1 when the HLLD and HLL fluxes differ by
-more than 1e-3 in some scaled component.  The network 16 -> 32 -> 32 -> 1 is
+The data are faces the method itself produces: runs of a periodic box (HLLD
+everywhere) are paused at a few snapshots, and at each a seeded random set of
+faces is sampled with ``mhd_dump_faces`` on an FP64 handle holding the
+snapshot -- 16 features of the reconstructed states, and the label 1 when the
+HLLD and HLL fluxes differ by more than 1e-3 in some scaled component.  The network 16 -> 32 -> 32 -> 1 is
 trained with this library's BF16 tensor-core kernels (``mlp_backward``,
 ``mlp_adam`` on FP32 master weights); PyTorch only holds the device buffers
 and draws the minibatch indices.  The threshold tau is the largest one that
@@ -48,12 +48,16 @@ def he_init(seed: int) -> np.ndarray:
         np.float32)
 
 
-def collect_faces(box, nfaces: int, snapshots=(2, 6, 12, 24), seed: int = 5, precision="fp64") -> FaceSet:
-    """Run ``box`` with HLLD at its CFL dt and sample nfaces / len(snapshots)
-    random faces at each snapshot (total steps taken so far)."""
+def collect_faces(box, nfaces: int, snapshots=(25, 50, 100, 200), seed: int = 5,
+                  evolve: str = "mixed") -> FaceSet:
+    """Run ``box`` with HLLD at its CFL dt (in the ``evolve`` precision) and
+    sample nfaces / len(snapshots) random faces at each snapshot (total steps
+    taken so far).  Features and labels always come from an FP64 handle
+    holding the snapshot's state."""
     import torch
-    s = mhd.Solver(box, precision=precision, riemann="hlld")
-    s.set_state(box.cell, box.face)
+    run = mhd.Solver(box, precision=evolve, riemann="hlld")
+    run.set_state(box.cell, box.face)
+    lab = run if evolve == "fp64" else mhd.Solver(box, precision="fp64", riemann="hlld")
     nall = 3 * box.nx * box.ny * box.nz
     per = int(math.ceil(nfaces / len(snapshots)))
     gen = torch.Generator(device="cuda").manual_seed(seed)
@@ -62,13 +66,18 @@ def collect_faces(box, nfaces: int, snapshots=(2, 6, 12, 24), seed: int = 5, pre
     done, info = 0, []
     for i, target in enumerate(snapshots):
         if target > done:
-            s.step(-1.0, target - done)
+            run.step(-1.0, target - done)
             done = target
+        if lab is not run:
+            c, f = run.get_state()
+            lab.set_state(c, f)
         ids = torch.randint(0, nall, (per,), device="cuda", generator=gen, dtype=torch.int64)
         xs, ys = X[i * per:(i + 1) * per], y[i * per:(i + 1) * per]
-        mhd.mhd_dump_faces(s.h, ids.data_ptr(), per, xs.data_ptr(), ys.data_ptr())
+        mhd.mhd_dump_faces(lab.h, ids.data_ptr(), per, xs.data_ptr(), ys.data_ptr())
         info.append((done, per, float(ys.mean())))
-    s.close()
+    if lab is not run:
+        lab.close()
+    run.close()
     return FaceSet(X[:nfaces].contiguous(), y[:nfaces].contiguous(), info)
 
 
@@ -122,14 +131,22 @@ def train(faces: FaceSet, steps: int = 3000, batch: int = 16384, lr: float = 3e-
     l0 = bce(sw.logits(Xv), yv)
     t0 = time.perf_counter()
     ntr = Xt.shape[0]
+    # when faces that need HLLD are rare, half of every minibatch is drawn
+    # from them (the threshold is then chosen on the natural distribution)
+    pos = torch.nonzero(yt > 0.5).flatten()
+    balance = 0 < pos.numel() < 0.25 * ntr
     for it in range(steps):
         idx = torch.randint(0, ntr, (batch,), device="cuda", generator=gen)
+        if balance:
+            k = torch.randint(0, pos.numel(), (batch // 2,), device="cuda", generator=gen)
+            idx[: batch // 2] = pos[k]
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / steps))
         sw.step(Xt[idx].contiguous(), yt[idx].contiguous(), max(lr_t, lr * 1e-2))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     zv = sw.logits(Xv)
     rep = {"faces": n, "train": int(ntr), "val": int(nval), "label1_frac": float(faces.y.mean()),
+           "val_label1": int((yv > 0.5).sum()), "balanced_batches": bool(balance),
            "val_loss_init": l0, "val_loss": bce(zv, yv), "steps": steps, "batch": batch, "train_s": t_train}
     return sw, (Xv, yv, zv), rep
 
@@ -146,7 +163,7 @@ def choose_tau(zv, yv, recall: float = 0.99):
         zt = float(torch.sort(z1).values[k])
     zt32 = float(np.float32(zt))
     tau = 1.0 / (1.0 + math.exp(-zt32))
-    tau = min(max(tau, 1e-6), 1.0 - 1e-6)
+    tau = min(max(tau, 1e-30), 1.0 - 1e-12)
     # the kernels compare the FP32 logit with the FP32 logit of tau
     zk = float(np.float32(math.log(tau / (1.0 - tau))))
     hlld = zv >= zk
@@ -155,13 +172,13 @@ def choose_tau(zv, yv, recall: float = 0.99):
 
 
 def train_switch(n: int = 256, nfaces: int = 10_000_000, seed: int = 5, steps: int = 3000, batch: int = 16384,
-                 recall: float = 0.99, snapshots=(2, 6, 12, 24)):
+                 recall: float = 0.99, snapshots=(25, 50, 100, 200), evolve: str = "mixed"):
     """The whole pipeline on a turbulence box of n^3 cells (the
     decaying-turbulence start with ``seed``): faces, training, threshold.
     Returns (Switch, tau, report)."""
     box = turbulence_3d(n, seed=seed)
     t0 = time.perf_counter()
-    faces = collect_faces(box, nfaces, snapshots=snapshots, seed=seed)
+    faces = collect_faces(box, nfaces, snapshots=snapshots, seed=seed, evolve=evolve)
     t_collect = time.perf_counter() - t0
     sw, (Xv, yv, zv), rep = train(faces, steps=steps, batch=batch, seed=seed)
     tau, trep = choose_tau(zv, yv, recall)
