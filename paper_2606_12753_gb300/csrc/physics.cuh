@@ -53,13 +53,14 @@ __host__ __device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
   return rsqrt_(R(0.5) * (s + rsqrt_(disc)));
 }
 
-// Physical flux along the normal (7 components, rotated order).
+// Physical flux along the normal (7 components, rotated order); igm1 is
+// 1/(gamma - 1), taken once per solve so the energy needs no division.
 template <typename R>
-__host__ __device__ __forceinline__ void phys_flux(const R* w, R bn, R gamma, R* f) {
+__host__ __device__ __forceinline__ void phys_flux_i(const R* w, R bn, R igm1, R* f) {
   R rho = w[0], u = w[1], v = w[2], ww = w[3], p = w[4], by = w[5], bz = w[6];
   R b2 = bn * bn + by * by + bz * bz;
   R pt = p + R(0.5) * b2;
-  R e = p / (gamma - R(1)) + R(0.5) * rho * (u * u + v * v + ww * ww) + R(0.5) * b2;
+  R e = p * igm1 + R(0.5) * rho * (u * u + v * v + ww * ww) + R(0.5) * b2;
   R vb = u * bn + v * by + ww * bz;
   R mu = rho * u;
   f[0] = mu;
@@ -72,8 +73,13 @@ __host__ __device__ __forceinline__ void phys_flux(const R* w, R bn, R gamma, R*
 }
 
 template <typename R>
-__host__ __device__ __forceinline__ R total_energy(const R* w, R bn, R gamma) {
-  return w[4] / (gamma - R(1)) + R(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
+__host__ __device__ __forceinline__ void phys_flux(const R* w, R bn, R gamma, R* f) {
+  phys_flux_i(w, bn, R(1) / (gamma - R(1)), f);
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ R total_energy_i(const R* w, R bn, R igm1) {
+  return w[4] * igm1 + R(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
          R(0.5) * (bn * bn + w[5] * w[5] + w[6] * w[6]);
 }
 
@@ -83,15 +89,16 @@ __host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn
   R cl = fast_speed(wl, bn, gamma), cr = fast_speed(wr, bn, gamma);
   R cm = rmax(cl, cr);
   if (cmax) *cmax = cm;
+  const R ig = R(1) / (gamma - R(1));
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
-  if (sl >= R(0)) { phys_flux(wl, bn, gamma, f); return; }
-  if (sr <= R(0)) { phys_flux(wr, bn, gamma, f); return; }
+  if (sl >= R(0)) { phys_flux_i(wl, bn, ig, f); return; }
+  if (sr <= R(0)) { phys_flux_i(wr, bn, ig, f); return; }
   R fl[7], fr[7];
-  phys_flux(wl, bn, gamma, fl);
-  phys_flux(wr, bn, gamma, fr);
-  R ul[7] = {wl[0], wl[0] * wl[1], wl[0] * wl[2], wl[0] * wl[3], total_energy(wl, bn, gamma), wl[5], wl[6]};
-  R ur[7] = {wr[0], wr[0] * wr[1], wr[0] * wr[2], wr[0] * wr[3], total_energy(wr, bn, gamma), wr[5], wr[6]};
+  phys_flux_i(wl, bn, ig, fl);
+  phys_flux_i(wr, bn, ig, fr);
+  R ul[7] = {wl[0], wl[0] * wl[1], wl[0] * wl[2], wl[0] * wl[3], total_energy_i(wl, bn, ig), wl[5], wl[6]};
+  R ur[7] = {wr[0], wr[0] * wr[1], wr[0] * wr[2], wr[0] * wr[3], total_energy_i(wr, bn, ig), wr[5], wr[6]};
   R inv = R(1) / (sr - sl);
 #pragma unroll
   for (int q = 0; q < 7; ++q) f[q] = (sr * fl[q] - sl * fr[q] + sl * sr * (ur[q] - ul[q])) * inv;
@@ -100,11 +107,18 @@ __host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn
 // Star state of one side (Miyoshi & Kusano eqs. 43-48).
 template <typename R>
 struct Star {
-  R rho, v, w, by, bz, e, vb, sq;
+  R rho, v, w, by, bz, e, vb, sq, isq;   // sq = sqrt(rho*), isq = 1/sqrt(rho*)
 };
 
 template <typename R>
-__host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R gamma, R s, R sm, R pts) {
+__host__ __device__ __forceinline__ R rrsqrt_(R x);
+template <>
+__host__ __device__ __forceinline__ double rrsqrt_<double>(double x) { return rsqrt(x); }
+template <>
+__host__ __device__ __forceinline__ float rrsqrt_<float>(float x) { return rsqrtf(x); }
+
+template <typename R>
+__host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, R s, R sm, R pts) {
   Star<R> st;
   R rho = w[0], u = w[1], v = w[2], ww = w[3], by = w[5], bz = w[6];
   R sd = s - u;
@@ -128,9 +142,10 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R gamma,
   R vb = u * bn + v * by + ww * bz;
   st.vb = sm * bn + st.v * st.by + st.w * st.bz;
   R pt = w[4] + R(0.5) * (bn2 + by * by + bz * bz);
-  R e = total_energy(w, bn, gamma);
+  R e = total_energy_i(w, bn, igm1);
   st.e = (sd * e - pt * u + pts * sm + bn * (vb - st.vb)) * inv_ssm;
-  st.sq = rsqrt_(st.rho);
+  st.isq = rrsqrt_<R>(st.rho);
+  st.sq = st.rho * st.isq;
   return st;
 }
 
@@ -142,28 +157,29 @@ __host__ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R b
   R cl = fast_speed(wl, bn, gamma), cr = fast_speed(wr, bn, gamma);
   R cm = rmax(cl, cr);
   if (cmax) *cmax = cm;
+  const R ig = R(1) / (gamma - R(1));
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
-  if (sl > R(0)) { phys_flux(wl, bn, gamma, f); return; }
-  if (sr < R(0)) { phys_flux(wr, bn, gamma, f); return; }
+  if (sl > R(0)) { phys_flux_i(wl, bn, ig, f); return; }
+  if (sr < R(0)) { phys_flux_i(wr, bn, ig, f); return; }
   R ptl = wl[4] + R(0.5) * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6]);
   R ptr = wr[4] + R(0.5) * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6]);
   R sdl = sl - wl[1], sdr = sr - wr[1];
   R sm = (sdr * wr[0] * wr[1] - sdl * wl[0] * wl[1] - ptr + ptl) / (sdr * wr[0] - sdl * wl[0]);
   R pts = ptl + wl[0] * sdl * (sm - wl[1]);
-  Star<R> L = star_side(wl, bn, gamma, sl, sm, pts);
-  Star<R> Rr = star_side(wr, bn, gamma, sr, sm, pts);
+  Star<R> L = star_side(wl, bn, ig, sl, sm, pts);
+  Star<R> Rr = star_side(wr, bn, ig, sr, sm, pts);
   R abn = rabs(bn);
-  R ssl = sm - abn / L.sq;
-  R ssr = sm + abn / Rr.sq;
+  R ssl = sm - abn * L.isq;
+  R ssr = sm + abn * Rr.isq;
   const bool left = sm >= R(0);
   const R* w = left ? wl : wr;
   const Star<R>& S = left ? L : Rr;
   R so = left ? sl : sr;
   bool dbl = left ? (ssl < R(0)) : (ssr >= R(0));
   R fo[7];
-  phys_flux(w, bn, gamma, fo);
-  R uo[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], total_energy(w, bn, gamma), w[5], w[6]};
+  phys_flux_i(w, bn, ig, fo);
+  R uo[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], total_energy_i(w, bn, ig), w[5], w[6]};
   R us[7] = {S.rho, S.rho * sm, S.rho * S.v, S.rho * S.w, S.e, S.by, S.bz};
 #pragma unroll
   for (int q = 0; q < 7; ++q) f[q] = fo[q] + so * (us[q] - uo[q]);
