@@ -99,7 +99,7 @@ __device__ __forceinline__ StageArgs box_stage_args(const BatchArgs& ba, const B
 }
 
 template <int PREC, int TX, int TY>
-__global__ void __launch_bounds__(256) batch_kernel(BatchArgs ba) {
+__global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 3) batch_kernel(BatchArgs ba) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned epoch = 0;
   for (int step = 0; step < ba.nsteps; ++step) {

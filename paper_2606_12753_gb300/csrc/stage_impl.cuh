@@ -181,55 +181,22 @@ struct StageKernel {
   }
 
   // ---------------------------------------------------------------- phase B
-  template <int D>
-  static __device__ __forceinline__ void face(const Geo& g, R* sm, const R (&c)[4][7], R bn, R* H, R* C, int n,
-                                              int out) {
-    R wl[7], wr[7], f[7], cm;
-    plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
-    const R gam = (R)g.gamma;
-    if (g.riemann == 1) hll_flux(wl, wr, bn, gam, f, &cm);
-    else hlld_flux(wl, wr, bn, gam, f, &cm);
-    // hydro flux back in (rho, mx, my, mz, E) order
-    H[0 * n + out] = f[0];
-    H[(1 + D) * n + out] = f[1];
-    H[(1 + (D + 1) % 3) * n + out] = f[2];
-    H[(1 + (D + 2) % 3) * n + out] = f[3];
-    H[4 * n + out] = f[4];
-    // CT parts: EMF of the t2 edge (-F(B_t1)), of the t1 edge (+F(B_t2)), orienting mass flux
-    C[out] = -f[5];
-    C[n + out] = f[6];
-    C[2 * n + out] = oriented_mass_flux(f[0], wl[0], wr[0], cm, (R)g.deadband);
-  }
-
+  // Every flux item (z-faces k+1/2, x- and y-faces of plane q) runs through
+  // one reconstruction + Riemann + store path: only the stencil gather
+  // depends on the face's axis, so a warp whose items straddle two axes
+  // still solves once.
   static __device__ __forceinline__ void fluxes(const Geo& g, R* sm, int k, int q, bool with_z) {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
-    const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
-    const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
+    const R gam = (R)g.gamma;
     for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
-      R c[4][7];
-      if (w < nZ) {
-        const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
-        const int r = (i + 2) + W * (j + 2);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) gather<2>(sm + T::oP + ((k - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
-        const R bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
-        face<2>(g, sm, c, bn, sm + T::oHZ, sm + T::oZC, T::nZ, w);
-      } else if (w < nZ + T::nX) {
-        const int o = w - nZ;
-        const int i = o % (TX + 1), j = o / (TX + 1) - 1;
-        const int r = (i + 2) + W * (j + 2);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) gather<0>(Pq, T::nR, r - 2 + s, c[s]);
-        face<0>(g, sm, c, BNq[r], sm + T::oHX, sm + T::oXC + (q & 1) * 3 * T::nX, T::nX, o);
-      } else {
-        const int o = w - nZ - T::nX;
-        const int i = o % (TX + 2) - 1, j = o / (TX + 2);
-        const int r = (i + 2) + W * (j + 2);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) gather<1>(Pq, T::nR, r + (s - 2) * W, c[s]);
-        face<1>(g, sm, c, BNq[T::nR + r], sm + T::oHY, sm + T::oYC + (q & 1) * 3 * T::nY, T::nY, o);
-      }
+      R c[4][7], wl[7], wr[7], f[7], bn, cm;
+      int o;
+      const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
+      plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+      if (g.riemann == 1) hll_flux(wl, wr, bn, gam, f, &cm);
+      else hlld_flux(wl, wr, bn, gam, f, &cm);
+      store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
     }
     cell_emf(sm, q);
   }
@@ -285,7 +252,9 @@ struct StageKernel {
     return 1;
   }
 
-  // Store the flux of slot o on axis D (same layout as face<D>).
+  // Store the flux of slot o on axis D: the hydro fluxes back in (rho, mx,
+  // my, mz, E) order; the EMFs of the t2 edge (-F(B_t1)) and of the t1 edge
+  // (+F(B_t2)); the mass flux that orients the upwind EMF.
   template <int D>
   static __device__ __forceinline__ void store_flux(const Geo& g, R* sm, int q, int o, const R* f, R cm, R rl, R rr) {
     R* H;
@@ -672,7 +641,7 @@ struct StageKernel {
 };
 
 template <int PREC, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(256) stage_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 3) stage_kernel(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY>::run_item(g, a, blockIdx.x, smem_raw);
 }
