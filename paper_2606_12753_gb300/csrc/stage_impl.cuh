@@ -641,7 +641,7 @@ struct StageKernel {
 };
 
 template <int PREC, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 3) stage_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(256, PREC == P_FP64 ? (TX * TY <= 64 ? 2 : 1) : 3) stage_kernel(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY>::run_item(g, a, blockIdx.x, smem_raw);
 }

@@ -59,9 +59,10 @@ def test_learned_switch_reduces_to_each_solver(precision):
         blk = _block(torch, _params(0, zero=True, b3=b3))
         (c, f), st = _run(box, precision, "learned", 2, blk, dt=dt)
         (c0, f0), _ = _run(box, precision, pure, 2, dt=dt)
-        assert np.array_equal(c, c0), (precision, pure)
-        for d in range(3):
-            assert np.array_equal(f[d], f0[d]), (precision, pure, d)
+        # the same solver on every face; two kernels compiled separately may
+        # contract a multiply-add differently, so the states agree to rounding
+        errs = state_errors(c, f, c0, f0)
+        assert max(errs.values()) <= (1e-13 if precision == "fp64" else 1e-6), (precision, pure, errs)
         # every face evaluation (halo faces recomputed by neighbouring tiles
         # included) took the chosen solver
         hll, hlld = st["faces_hll"], st["faces_hlld"]
