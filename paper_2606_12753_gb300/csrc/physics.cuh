@@ -35,22 +35,36 @@ __host__ __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 template <typename R>
 __host__ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
   R dm = q0 - qm, dp = qp - q0;
-  R a = R(2) * rabs(dm), b = R(2) * rabs(dp), c = R(0.5) * rabs(dm + dp);
-  R m = rmin(rmin(a, b), c);
+  // min(2|dm|, 2|dp|, |dm+dp|/2): doubling is exact, so 2 min(|dm|, |dp|)
+  // is the same value with one multiply fewer
+  R m = rmin(R(2) * rmin(rabs(dm), rabs(dp)), R(0.5) * rabs(dm + dp));
   R s = dp > R(0) ? m : -m;
   return dm * dp > R(0) ? s : R(0);
 }
 
-// Fast magnetosonic speed along the normal; w = (rho, vn, vt1, vt2, p, Bt1, Bt2).
+// Fast magnetosonic speed along the normal; w = (rho, vn, vt1, vt2, p, Bt1,
+// Bt2); rinv = 1/rho.
 template <typename R>
-__host__ __device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
-  R rinv = R(1) / w[0];
+__host__ __device__ __forceinline__ R fast_speed_r(const R* w, R bn, R gamma, R rinv) {
   R a2 = gamma * w[4] * rinv;
   R b2 = (bn * bn + w[5] * w[5] + w[6] * w[6]) * rinv;
   R s = a2 + b2;
   R disc = s * s - R(4) * a2 * bn * bn * rinv;
   disc = disc > R(0) ? disc : R(0);
   return rsqrt_(R(0.5) * (s + rsqrt_(disc)));
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
+  return fast_speed_r(w, bn, gamma, R(1) / w[0]);
+}
+
+// Fast speeds of both states of a face from one reciprocal of rho_L rho_R.
+template <typename R>
+__host__ __device__ __forceinline__ void fast_speeds(const R* wl, const R* wr, R bn, R gamma, R& cl, R& cr) {
+  const R r = R(1) / (wl[0] * wr[0]);
+  cl = fast_speed_r(wl, bn, gamma, wr[0] * r);
+  cr = fast_speed_r(wr, bn, gamma, wl[0] * r);
 }
 
 // Physical flux along the normal (7 components, rotated order); igm1 is
@@ -83,13 +97,14 @@ __host__ __device__ __forceinline__ R total_energy_i(const R* w, R bn, R igm1) {
          R(0.5) * (bn * bn + w[5] * w[5] + w[6] * w[6]);
 }
 
-// HLL flux.
+// HLL flux; ig = 1/(gamma - 1).
 template <typename R>
-__host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn, R gamma, R* f, R* cmax = nullptr) {
-  R cl = fast_speed(wl, bn, gamma), cr = fast_speed(wr, bn, gamma);
+__host__ __device__ __forceinline__ void hll_flux_g(const R* wl, const R* wr, R bn, R gamma, R ig, R* f,
+                                                    R* cmax = nullptr) {
+  R cl, cr;
+  fast_speeds(wl, wr, bn, gamma, cl, cr);
   R cm = rmax(cl, cr);
   if (cmax) *cmax = cm;
-  const R ig = R(1) / (gamma - R(1));
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
   if (sl >= R(0)) { phys_flux_i(wl, bn, ig, f); return; }
@@ -102,6 +117,11 @@ __host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn
   R inv = R(1) / (sr - sl);
 #pragma unroll
   for (int q = 0; q < 7; ++q) f[q] = (sr * fl[q] - sl * fr[q] + sl * sr * (ur[q] - ul[q])) * inv;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn, R gamma, R* f, R* cmax = nullptr) {
+  hll_flux_g(wl, wr, bn, gamma, R(1) / (gamma - R(1)), f, cmax);
 }
 
 // Star state of one side (Miyoshi & Kusano eqs. 43-48).
@@ -122,16 +142,20 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
   Star<R> st;
   R rho = w[0], u = w[1], v = w[2], ww = w[3], by = w[5], bz = w[6];
   R sd = s - u;
-  R inv_ssm = R(1) / (s - sm);
-  st.rho = rho * sd * inv_ssm;
-  R num = rho * sd * (s - sm);
+  R ssm = s - sm;
+  R num = rho * sd * ssm;
   R bn2 = bn * bn;
   R den = num - bn2;
   R scale = rmax(rabs(num), bn2);
+  R inv_ssm;
   if (rabs(den) <= Eps<R>::degen * scale) {
+    inv_ssm = R(1) / ssm;
     st.v = v; st.w = ww; st.by = by; st.bz = bz;
   } else {
-    R iden = R(1) / den;
+    // 1/(S - S_M) and 1/den from one reciprocal of their product
+    const R r = R(1) / (ssm * den);
+    inv_ssm = den * r;
+    R iden = ssm * r;
     R c1 = bn * (sm - u) * iden;
     R c2 = (rho * sd * sd - bn2) * iden;
     st.v = v - by * c1;
@@ -139,6 +163,7 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
     st.by = by * c2;
     st.bz = bz * c2;
   }
+  st.rho = rho * sd * inv_ssm;
   R vb = u * bn + v * by + ww * bz;
   st.vb = sm * bn + st.v * st.by + st.w * st.bz;
   R pt = w[4] + R(0.5) * (bn2 + by * by + bz * bz);
@@ -153,11 +178,12 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
 // L, L*, L**, R**, R*, R; sign(0) = 0; degenerate star states (den ~ 0)
 // keep the outer tangential values.
 template <typename R>
-__host__ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R bn, R gamma, R* f, R* cmax = nullptr) {
-  R cl = fast_speed(wl, bn, gamma), cr = fast_speed(wr, bn, gamma);
+__host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R bn, R gamma, R ig, R* f,
+                                                     R* cmax = nullptr) {
+  R cl, cr;
+  fast_speeds(wl, wr, bn, gamma, cl, cr);
   R cm = rmax(cl, cr);
   if (cmax) *cmax = cm;
-  const R ig = R(1) / (gamma - R(1));
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
   if (sl > R(0)) { phys_flux_i(wl, bn, ig, f); return; }
@@ -197,6 +223,11 @@ __host__ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R b
 #pragma unroll
     for (int q = 0; q < 7; ++q) f[q] += sso * (uss[q] - us[q]);
   }
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R bn, R gamma, R* f, R* cmax = nullptr) {
+  hlld_flux_g(wl, wr, bn, gamma, R(1) / (gamma - R(1)), f, cmax);
 }
 
 // Mass flux that orients the upwind EMF average: the face mass flux, or 0

@@ -189,13 +189,14 @@ struct StageKernel {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
     const R gam = (R)g.gamma;
+    const R ig = R(1) / (gam - R(1));
     for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
       R c[4][7], wl[7], wr[7], f[7], bn, cm;
       int o;
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
       plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
-      if (g.riemann == 1) hll_flux(wl, wr, bn, gam, f, &cm);
-      else hlld_flux(wl, wr, bn, gam, f, &cm);
+      if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
+      else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
     }
     cell_emf(sm, q);
@@ -303,6 +304,7 @@ struct StageKernel {
     const float* master = a.mlp;
     const uint16_t* wb =
         reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(a.mlp) + MLP_MASTER_BYTES);
+    const R ig = R(1) / (gam - R(1));
     int* cnt = qcnt + 2 * (q & 1);   // [0] HLL items (front), [1] HLLD items (back)
     const bool record = a.choices != nullptr && q >= kb && q < ke;
     for (int base = threadIdx.x & ~31; base < nitems; base += blockDim.x) {
@@ -356,10 +358,10 @@ struct StageKernel {
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
       plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
       if (t < nhll) {
-        hll_flux(wl, wr, bn, gam, f, &cm);
+        hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
         ++nh;
       } else {
-        hlld_flux(wl, wr, bn, gam, f, &cm);
+        hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
         ++nd;
       }
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
