@@ -73,23 +73,42 @@ def peaks():
 
 
 class ClockSampler:
-    def __init__(self, index):
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms with
+    timestamps.  Started before the warm-up (it waits for its first sample),
+    marked around the timed region; the summary keeps the samples inside the
+    timed region, widened back into the warm-up that ran just before it when
+    fewer than 3 fell inside (the window used is reported)."""
+
+    def __init__(self, index, interval_ms=50):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
+        self.t0 = self.t1 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
 
-    def __enter__(self):
+    def start(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu=timestamp,{CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-i", str(self.index),
+                                          "-lms", str(self.interval_ms)], stdout=self.f, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 3.0
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
 
-    def __exit__(self, *a):
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
         if self.proc is not None:
+            time.sleep(self.interval_ms / 1000.0)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -97,30 +116,44 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
+    def _samples(self):
+        import datetime
+        out = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                out.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        return out
+
     def summary(self):
-        if self.proc is None:
+        if self.proc is None or self.t0 is None or self.t1 is None:
             return None
-        sm, mx, reasons = [], [], set()
-        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
-            for line in open(self.path):
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for nm, val in zip(names[1:], parts[5:9]):
-                    if val.lower().startswith("active"):
-                        reasons.add(nm)
+            samples = self._samples()
         except FileNotFoundError:
             return None
-        if not sm:
+        lo, window = self.t0, "timed region"
+        inside = [x for x in samples if lo <= x[0] <= self.t1]
+        while len(inside) < 3 and lo > self.t0 - 2.0:
+            lo -= 0.1
+            inside = [x for x in samples if lo <= x[0] <= self.t1]
+            window = f"timed region + the preceding {self.t0 - lo:.1f} s of warm-up"
+        if not inside:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for x in inside:
+            for nm, val in zip(names, x[3]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(x[1] for x in inside), "sm_max_mhz": max(x[2] for x in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+                "timed_s": round(self.t1 - self.t0, 3)}
 
 
 def traffic_from_profiles(kernel_tag):
@@ -265,18 +298,21 @@ def run_ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    clk = ClockSampler(local).start()
     solver.step_async(-1.0, args.warmup)
     st_w = solver.stats()
     solver.set_profiling(True)
     solver.profile()
     barrier()
-    with ClockSampler(local) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        solver.step_async(-1.0, args.steps)
-        e1.record(stream)
-        stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clk.mark_start()
+    e0.record(stream)
+    solver.step_async(-1.0, args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    clk.mark_end()
+    clk.stop()
     barrier()
     ms_total = e0.elapsed_time(e1)
     stage_ms, launches = solver.profile()
@@ -436,15 +472,18 @@ def run_batch(args):
         batch.set_state(i, b.cell, b.face)
     cache = os.environ.get("MHD_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "mhd_autotune.jsonl")
     tile, tune_ms = batch.autotune(trial_steps=3, cache_path=cache)
+    clk = ClockSampler(local).start()
     batch.step(-1.0, args.warmup)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        batch.step_async(-1.0, args.steps)
-        e1.record(stream)
-        stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clk.mark_start()
+    e0.record(stream)
+    batch.step_async(-1.0, args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    clk.mark_end()
+    clk.stop()
     ms_total = e0.elapsed_time(e1)
     st = batch.stats()
     if st["status"] != 0:

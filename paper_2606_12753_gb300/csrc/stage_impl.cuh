@@ -45,7 +45,7 @@ struct Tile {
   static constexpr int oEZ = oEXY + 2 * 2 * nE;
   static constexpr int oDU = oEZ + nE;
   static constexpr int nRtot = oDU + 2 * 5 * nC;
-  // new face values (type S): NBX[nE], NBY[nE], NBZ[2][nC]
+  // new face values (type S): NBX[nE], NBY[nE], NBZ[2][nC] (z-faces by parity)
   static constexpr int nS = 2 * nE + 2 * nC;
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
@@ -462,7 +462,7 @@ struct StageKernel {
 
   // ---------------------------------------------------------------- phase D
   static __device__ __forceinline__ void new_faces(const Geo& g, const StageArgs& a, R* sm, S* NB, double dt,
-                                                   int gi0, int gj0, int k) {
+                                                   int gi0, int gj0, int k, int kb, int ke) {
     const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1], idz = (R)g.inv_d[2];
     const R* EZ = sm + T::oEZ;
     const R* EX0 = sm + T::oEXY + (k & 1) * 2 * T::nE;   // k-1/2
@@ -495,20 +495,26 @@ struct StageKernel {
         NBY[e] = v;
         if ((j < TY && gj < ny) || (outy && gj == ny)) emit(a, f, l, v);
       }
-      // B_z on the faces k-1/2 (owned) and k+1/2 of cell (i, j)
+      // B_z on the faces k-1/2 and k+1/2 of cell (i, j), kept by face parity
+      // (slot m & 1 holds face m): face k+1/2 computed here is face k-1/2 of
+      // the next plane, so only the first plane of a chunk computes its lower
+      // face.  A face is emitted by the plane whose lower face it is, and the
+      // top face of an outflow axis by the last plane.
       if (i < TX && j < TY && gi < nx && gj < ny) {
         const int c = i + TX * j;
-        const long long flo = zface_index(g, gi, gj, k);
-        const R llo = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
-        const S vlo = advance(a, flo, llo, dt);
-        NBZ[c] = vlo;
-        emit(a, flo, llo, vlo);
+        if (k == kb) {
+          const long long flo = zface_index(g, gi, gj, k);
+          const R llo = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
+          const S vlo = advance(a, flo, llo, dt);
+          NBZ[(k & 1) * T::nC + c] = vlo;
+          emit(a, flo, llo, vlo);
+        }
         const int khi = k + 1 == nz && !outz ? 0 : k + 1;
         const long long fhi = zface_index(g, gi, gj, khi);
         const R lhi = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
         const S vhi = advance(a, fhi, lhi, dt);
-        NBZ[T::nC + c] = vhi;
-        if (outz && k + 1 == nz) emit(a, fhi, lhi, vhi);
+        NBZ[((k + 1) & 1) * T::nC + c] = vhi;
+        if (k + 1 < ke || (outz && k + 1 == nz)) emit(a, fhi, lhi, vhi);
       }
     }
   }
@@ -540,7 +546,8 @@ struct StageKernel {
       R w[NW];
       int hr, hp;
       recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], (double)NBX[e], (double)NBX[e + 1], (double)NBY[e],
-                    (double)NBY[e + (TX + 1)], (double)NBZ[c], (double)NBZ[T::nC + c], w, hr, hp);
+                    (double)NBY[e + (TX + 1)], (double)NBZ[(k & 1) * T::nC + c],
+                    (double)NBZ[((k + 1) & 1) * T::nC + c], w, hr, hp);
       nrho += hr;
       np += hp;
       if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
@@ -564,10 +571,11 @@ struct StageKernel {
     int* colc = reinterpret_cast<int*>(smem_raw + iOff);
     int* rowc = colc + W;
     int* qcnt = rowc + T::H;
-    // the HLLD queue of the learned switch lives in the new-face buffer,
-    // which is idle from the start of the flux phase to new_faces
+    // the HLLD queue of the learned switch lives in the x- and y-face part of
+    // the new-face buffer, which is idle from the start of the flux phase to
+    // new_faces (the z-face part carries face k+1/2 over to the next plane)
     unsigned short* queue = reinterpret_cast<unsigned short*>(NB);
-    static_assert((size_t)T::nItems * sizeof(unsigned short) <= (size_t)T::nS * sizeof(S), "queue does not fit");
+    static_assert((size_t)T::nItems * sizeof(unsigned short) <= (size_t)2 * T::nE * sizeof(S), "queue does not fit");
 
     int b = item;
     const int tile_x = b % g.ntx;
@@ -612,7 +620,7 @@ struct StageKernel {
       divergence_and_edges(g, sm, k);
       __syncthreads();
       if (k >= kb) {
-        new_faces(g, a, sm, NB, dt, gi0, gj0, k);
+        new_faces(g, a, sm, NB, dt, gi0, gj0, k, kb, ke);
         __syncthreads();
         new_cells(g, a, sm, NB, dt, gi0, gj0, k, nrho, np, bad, smax);
       }
