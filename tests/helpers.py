@@ -39,3 +39,24 @@ def state_errors(cell, face, ref_cell, ref_face):
     for d in range(3):
         errs[names[5 + d]] = rel_l1(face[d], ref_face[d], max(1e-3 * bnorm, 1e-4 * b_scale))
     return errs
+
+
+def subbox(cell, face, n, center, h, dx, gamma):
+    """Outflow sub-box of (2h+1)^3 cells around center = (i, j, k), cut from a
+    periodic state of n = (nx, ny, nz) cells (indices wrap).  Returns (Config,
+    cell, face) for the oracle."""
+    i, j, k = center
+    nx, ny, nz = n
+    xi = np.arange(i - h, i + h + 1) % nx
+    yj = np.arange(j - h, j + h + 1) % ny
+    zk = np.arange(k - h, k + h + 1) % nz
+    xf = np.arange(i - h, i + h + 2) % nx
+    yf = np.arange(j - h, j + h + 2) % ny
+    zf = np.arange(k - h, k + h + 2) % nz
+    c = np.ascontiguousarray(cell[:, zk][:, :, yj][:, :, :, xi])
+    bx = np.ascontiguousarray(face[0][zk][:, yj][:, :, xf])
+    by = np.ascontiguousarray(face[1][zk][:, yf][:, :, xi])
+    bz = np.ascontiguousarray(face[2][zf][:, yj][:, :, xi])
+    m = 2 * h + 1
+    cfg = O.Config(m, m, m, dx[0], dx[1], dx[2], gamma, 0.4, (O.OUTFLOW,) * 3)
+    return cfg, c, [bx, by, bz]

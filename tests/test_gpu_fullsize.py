@@ -1,0 +1,182 @@
+"""Parity at full size, in the launch configuration the benchmark times
+(turbulence 256^3, seed 2606, 16x8x32 tiles): sampled cells against the
+oracle.  The operator L(U) at a cell depends on the state within 2 cells of
+it, one RK2 step within 4 (pinned in test_oracle_locality.py); so the oracle,
+run on an outflow sub-box of radius 4 (operator) or 7 (step) cut from the
+full periodic state around the cell, gives that cell's exact result -- its
+ghosts never reach the centre.  Samples cover tile corners, chunk
+boundaries and the periodic seams, plus seeded random cells.  The step is
+compared on the turbulence start itself; the operator on a 256^3 smooth
+random state (every variable perturbed), because the turbulence start has
+uniform density and a solenoidal velocity, so its density rate is a
+rounding-level residual whose relative error says nothing.  Tolerance:
+relative L1 over the samples, 1e-12 (FP64) and 1e-5 (mixed) for the state
+after a step (vector components floored as in the suite's state metric);
+for the operator in FP32 bulk, 1e-5 x n/64 (see _operator_tol)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_12753_gb300 import inputs as I
+from helpers import subbox
+
+pytestmark = pytest.mark.gpu
+
+N = 256
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def box():
+    return I.turbulence_3d(N, seed=2606)
+
+
+@pytest.fixture(scope="module")
+def smooth():
+    return I.random_state((N, N, N), seed=2606, bc=(0, 0, 0), noise=0.0)
+
+
+def _samples(seed=2606, nrand=24):
+    edge = [0, 1, 15, 16, 127, 128, 254, 255]          # x tiles of 16
+    edge_y = [0, 7, 8, 127, 128, 255]                  # y tiles of 8
+    edge_z = [0, 31, 32, 63, 64, 255]                  # z chunks of 32
+    rng = np.random.default_rng(seed)
+    pts = [(edge[a % len(edge)], edge_y[a % len(edge_y)], edge_z[a % len(edge_z)]) for a in range(12)]
+    pts += [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(nrand)]
+    return pts
+
+
+def _subbox(box, center, h):
+    return subbox(box.cell, box.face, (N, N, N), center, h, (box.dx, box.dy, box.dz), box.gamma)
+
+
+def _rel_l1(got, ref):
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    return float(np.abs(got - ref).sum() / max(np.abs(ref).sum(), 1e-300))
+
+
+def _compare(got_c, ref_c, got_f, ref_f, tol, what, state=False):
+    """Relative L1 per variable over the samples.  For states (state=True) a
+    vector component is measured against max(its own L1, 1e-3 x the L1 of the
+    whole vector, 1e-4 x an energy scale), the suite's state metric, so that
+    B_x, B_y of the turbulence start (zero before the step) are not divided
+    by their own one-step increment."""
+    names = ["rho", "mx", "my", "mz", "E"]
+    floor_m = floor_b = 0.0
+    if state:
+        e = np.maximum(ref_c[:, 4], 0.0)
+        floor_m = max(1e-3 * float(np.abs(ref_c[:, 1:4]).sum()),
+                      1e-4 * float(np.sqrt(np.maximum(ref_c[:, 0], 0.0) * e).sum()))
+        floor_b = max(1e-3 * float(np.abs(ref_f).sum()), 1e-4 * float(np.sqrt(e).sum()))
+
+    def rel(g, r, floor):
+        return float(np.abs(np.asarray(g, np.float64) - r).sum() / max(np.abs(r).sum(), floor, 1e-300))
+
+    errs = {names[v]: rel(got_c[:, v], ref_c[:, v], floor_m if 1 <= v <= 3 else 0.0) for v in range(5)}
+    comps = "xyz"[3 - ref_f.shape[1]:]
+    errs.update({f"B{comps[d]}": rel(got_f[:, d], ref_f[:, d], floor_b) for d in range(ref_f.shape[1])})
+    assert max(errs.values()) <= tol, (what, errs)
+    return errs
+
+
+def _operator_tol(precision):
+    """L(U) is a difference of face fluxes over a cell width: its FP32 rounding
+    is ~eps x |F| / dx while its size is ~|F| k, so its relative error grows
+    linearly with the resolution.  The FP32 bar 1e-5 holds the operator at up
+    to 64 cells per axis (tests at that size); at n cells it is 1e-5 x n/64."""
+    return TOL[precision] * (max(1.0, N / 64.0) if precision != "fp64" else 1.0)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_operator_at_256_sampled(smooth, precision):
+    box = smooth
+    from paper_2606_12753_gb300 import mhd
+    s = mhd.Solver(box, precision=precision)
+    assert (s.cfg.tile_x, s.cfg.tile_y, s.cfg.tile_z) == (0, 0, 0)   # the default (bench) launch
+    s.set_state(box.cell, box.face)
+    gc, gf = s.rhs()
+    s.close()
+    got_c, ref_c, got_f, ref_f = [], [], [], []
+    h = 4
+    for (i, j, k) in _samples():
+        cfg, cell, face = _subbox(box, (i, j, k), h)
+        du, db = O.rhs(cfg, cell, face)
+        ref_c.append(du[:, h, h, h])
+        got_c.append(gc[:, k, j, i])
+        ref_f.append([db[0][h, h, h], db[1][h, h, h], db[2][h, h, h]])
+        got_f.append([gf[0][k, j, i], gf[1][k, j, i], gf[2][k, j, i]])
+    _compare(np.array(got_c), np.array(ref_c), np.array(got_f), np.array(ref_f), _operator_tol(precision),
+             f"L(U) {precision}")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("state", ["turbulence", "smooth"])
+def test_step_at_256_sampled(box, smooth, state, precision):
+    from paper_2606_12753_gb300 import mhd
+    start = box if state == "turbulence" else smooth
+    s = mhd.Solver(start, precision=precision)
+    s.set_state(start.cell, start.face)
+    dt = s.cfl_dt()
+    s.step(dt, 1)
+    c, f = s.get_state()
+    s.close()
+    got_c, ref_c, got_f, ref_f = [], [], [], []
+    h = 7
+    for (i, j, k) in _samples(nrand=12):
+        cfg, cell, face = _subbox(start, (i, j, k), h)
+        rc, rf = O.step_dts(cfg, cell, face, [dt])
+        ref_c.append(rc[:, h, h, h])
+        got_c.append(c[:, k, j, i])
+        ref_f.append([rf[0][h, h, h], rf[1][h, h, h], rf[2][h, h, h]])
+        got_f.append([f[0][k, j, i], f[1][k, j, i], f[2][k, j, i]])
+    got_c, ref_c, got_f, ref_f = map(np.array, (got_c, ref_c, got_f, ref_f))
+    if state == "turbulence" and precision != "fp64":
+        # B_x and B_y of the turbulence start are zero: after one step they are
+        # the step's increment alone, so they carry the operator's relative
+        # error; every other variable is held to the state tolerance
+        assert np.all(start.face[0] == 0) and np.all(start.face[1] == 0)
+        _compare(got_c, ref_c, got_f[:, 2:], ref_f[:, 2:], TOL[precision], f"step {state} {precision}", state=True)
+        for d in range(2):
+            e = np.abs(got_f[:, d] - ref_f[:, d]).sum() / np.abs(ref_f[:, d]).sum()
+            assert e <= _operator_tol(precision), (d, e)
+    else:
+        _compare(got_c, ref_c, got_f, ref_f, TOL[precision], f"step {state} {precision}", state=True)
+
+
+def test_learned_operator_at_256_sampled(smooth):
+    """The learned switch at full size (mixed): the kernel's own per-face
+    choices, cut out around each sample, drive the oracle's MASK operator."""
+    box = smooth
+    import torch
+    from oracle import mlp as M
+    from paper_2606_12753_gb300 import mhd
+    p = M.init_params(9)
+    rng = np.random.default_rng(10)
+    p["b1"] = 0.2 * rng.standard_normal(32)
+    p["b2"] = 0.2 * rng.standard_normal(32)
+    vec = M.flatten(p).astype(np.float32)
+    blk = torch.zeros(mhd.mlp_param_bytes(), dtype=torch.uint8, device="cuda")
+    mhd.mlp_init(blk.data_ptr(), vec)
+    s = mhd.Solver(box, precision="mixed", riemann="learned")
+    s.set_switch(blk.data_ptr(), 0.5)
+    s.set_state(box.cell, box.face)
+    ch = torch.full((3 * box.ncell,), 7, dtype=torch.uint8, device="cuda")
+    s.switch_choices(ch.data_ptr())
+    gc, gf = s.rhs()
+    s.close()
+    choice = ch.cpu().numpy().reshape(3, N, N, N)
+    assert set(np.unique(choice)) <= {0, 1} and 0.05 < choice.mean() < 0.95
+    got_c, ref_c, got_f, ref_f = [], [], [], []
+    h = 4
+    for (i, j, k) in _samples():
+        cfg, cell, face = _subbox(box, (i, j, k), h)
+        xi, yj, zk = [(np.arange(c - h, c + h + 1)) % N for c in (i, j, k)]
+        cfg.riemann = O.MASK
+        cfg.choice = np.ascontiguousarray(choice[:, zk][:, :, yj][:, :, :, xi]).reshape(-1)
+        du, db = O.rhs(cfg, cell, face)
+        ref_c.append(du[:, h, h, h])
+        got_c.append(gc[:, k, j, i])
+        ref_f.append([db[0][h, h, h], db[1][h, h, h], db[2][h, h, h]])
+        got_f.append([gf[0][k, j, i], gf[1][k, j, i], gf[2][k, j, i]])
+    _compare(np.array(got_c), np.array(ref_c), np.array(got_f), np.array(ref_f), _operator_tol("mixed"),
+             "learned L(U)")
