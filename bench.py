@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
+    p.add_argument("--switch-faces", type=int, default=10_000_000, help="training faces of the learned switch")
+    p.add_argument("--switch-steps", type=int, default=3000, help="Adam steps of the learned switch")
     return p.parse_args()
 
 
@@ -284,7 +286,8 @@ def run_ours(args):
         # training (not timed): faces of FP64 turbulence runs with seed 5,
         # the library's BF16 forward/backward and Adam kernels
         from paper_2606_12753_gb300 import switch_train as T
-        sw, tau, switch_rep = T.train_switch(n=args.n, nfaces=10_000_000, seed=5, steps=3000, batch=16384)
+        sw, tau, switch_rep = T.train_switch(n=args.n, nfaces=args.switch_faces, seed=5, steps=args.switch_steps,
+                                             batch=16384)
     stream = torch.cuda.Stream()
     solver = mhd.Solver(box, precision=args.precision, riemann="learned" if learned else "hlld", tile=tile,
                         stream=stream.cuda_stream)
