@@ -82,6 +82,8 @@ class Config:
     mlp: np.ndarray | None = None
     mlp_zt: float = 0.0
     choice: np.ndarray | None = None
+    # time integrator of step / step_dts: "rk2" (Heun) or "rk3" (Shu-Osher SSP)
+    integrator: str = "rk2"
 
     def c(self) -> _Cfg:
         mp = None
@@ -131,6 +133,8 @@ def lib():
         PF = _P * 3
         L.orc_step.restype = None
         L.orc_step.argtypes = [C.POINTER(_Cfg), PP, PF, C.c_double, C.POINTER(_Stats)]
+        L.orc_step_rk3.restype = None
+        L.orc_step_rk3.argtypes = [C.POINTER(_Cfg), PP, PF, C.c_double, C.POINTER(_Stats)]
         L.orc_rhs.restype = None
         L.orc_rhs.argtypes = [C.POINTER(_Cfg), PP, PF, PP, PF, C.POINTER(_Stats)]
         L.orc_cfl_dt.restype = C.c_double
@@ -221,6 +225,13 @@ def copy_state(cell, face):
     return np.array(cell, dtype=np.float64, order="C"), [np.array(f, dtype=np.float64, order="C") for f in face]
 
 
+def _stepper(cfg: Config):
+    if cfg.integrator == "rk3":
+        return lib().orc_step_rk3
+    assert cfg.integrator == "rk2", cfg.integrator
+    return lib().orc_step
+
+
 def step(cfg: Config, cell, face, dt: float, nsteps: int = 1, stats: Stats | None = None):
     """Advance ``nsteps`` RK2 steps with a fixed ``dt`` (dt <= 0: CFL dt each
     step).  Returns new (cell, face, dts); the inputs are left untouched."""
@@ -231,7 +242,7 @@ def step(cfg: Config, cell, face, dt: float, nsteps: int = 1, stats: Stats | Non
     dts = []
     for _ in range(nsteps):
         h = dt if dt > 0 else lib().orc_cfl_dt(C.byref(c), cp, fp)
-        lib().orc_step(C.byref(c), cp, fp, h, C.byref(st))
+        _stepper(cfg)(C.byref(c), cp, fp, h, C.byref(st))
         dts.append(h)
     if stats is not None:
         stats.add(st)
@@ -244,7 +255,7 @@ def step_dts(cfg: Config, cell, face, dts):
     c = cfg.c()
     cp, fp = _state_ptrs(cfg, cell, face)
     for h in dts:
-        lib().orc_step(C.byref(c), cp, fp, float(h), None)
+        _stepper(cfg)(C.byref(c), cp, fp, float(h), None)
     return cell, face
 
 

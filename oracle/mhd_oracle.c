@@ -738,6 +738,49 @@ void orc_step(const orc_cfg *c, double *cell[5], double *face[3], double dt, orc
   for (int d = 0; d < 3; ++d) { free(bs[d]); free(db[d]); }
 }
 
+/* One step of the three-stage strong-stability-preserving Runge-Kutta
+ * scheme of Shu & Osher (1988), in place:
+ *   U1      = U^n + dt L(U^n)
+ *   U2      = 3/4 U^n + 1/4 (U1 + dt L(U1))
+ *   U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
+ * for the 5 cell arrays and the 3 face arrays alike (the paper's default
+ * time integrator, Sec. 2.2). */
+void orc_step_rk3(const orc_cfg *c, double *cell[5], double *face[3], double dt, orc_stats *st) {
+  size_t nc = (size_t)c->nx * c->ny * c->nz;
+  size_t nfc[3] = {face_count(c, 0), face_count(c, 1), face_count(c, 2)};
+  double *u1[5], *b1[3], *u2[5], *b2[3], *du[5], *db[3];
+  for (int v = 0; v < 5; ++v) {
+    u1[v] = malloc(nc * sizeof(double));
+    u2[v] = malloc(nc * sizeof(double));
+    du[v] = malloc(nc * sizeof(double));
+  }
+  for (int d = 0; d < 3; ++d) {
+    b1[d] = malloc(nfc[d] * sizeof(double));
+    b2[d] = malloc(nfc[d] * sizeof(double));
+    db[d] = malloc(nfc[d] * sizeof(double));
+  }
+  spatial_operator(c, cell, face, du, db, st, NULL);
+  for (int v = 0; v < 5; ++v)
+    for (size_t s = 0; s < nc; ++s) u1[v][s] = cell[v][s] + dt * du[v][s];
+  for (int d = 0; d < 3; ++d)
+    for (size_t s = 0; s < nfc[d]; ++s) b1[d][s] = face[d][s] + dt * db[d][s];
+
+  spatial_operator(c, u1, b1, du, db, st, NULL);
+  for (int v = 0; v < 5; ++v)
+    for (size_t s = 0; s < nc; ++s) u2[v][s] = 0.75 * cell[v][s] + 0.25 * (u1[v][s] + dt * du[v][s]);
+  for (int d = 0; d < 3; ++d)
+    for (size_t s = 0; s < nfc[d]; ++s) b2[d][s] = 0.75 * face[d][s] + 0.25 * (b1[d][s] + dt * db[d][s]);
+
+  spatial_operator(c, u2, b2, du, db, st, NULL);
+  for (int v = 0; v < 5; ++v)
+    for (size_t s = 0; s < nc; ++s) cell[v][s] = cell[v][s] / 3.0 + 2.0 / 3.0 * (u2[v][s] + dt * du[v][s]);
+  for (int d = 0; d < 3; ++d)
+    for (size_t s = 0; s < nfc[d]; ++s) face[d][s] = face[d][s] / 3.0 + 2.0 / 3.0 * (b2[d][s] + dt * db[d][s]);
+
+  for (int v = 0; v < 5; ++v) { free(u1[v]); free(u2[v]); free(du[v]); }
+  for (int d = 0; d < 3; ++d) { free(b1[d]); free(b2[d]); free(db[d]); }
+}
+
 /* CFL time step dt = C / max over cells of sum_{d: n_d > 1} (|v_d| + c_f,d)/Delta_d,
  * the fast speed along d taken with the cell-centred B_d as the normal field. */
 double orc_cfl_dt(const orc_cfg *c, double *const cell[5], double *const face[3]) {

@@ -135,3 +135,28 @@ def test_brio_wu_self_convergence():
     # the far-field states are untouched at t = 0.1
     assert sols[400][:40] == pytest.approx(1.0, abs=1e-12)
     assert sols[400][-40:] == pytest.approx(0.125, abs=1e-12)
+
+
+@pytest.mark.parametrize("wave", ["fast", "alfven"])
+def test_rk3_is_third_order_in_time(wave):
+    """With the grid fixed, halving dt reduces the time-stepping error of
+    Shu-Osher SSP-RK3 by ~2^3 and of Heun RK2 by ~2^2: the error after 4
+    steps of dt (CFL 0.32) against a dt/32 run, for dt and dt/2.  A
+    small-amplitude wave keeps the right-hand side smooth along the
+    trajectory (limiter branches do not switch), where the integrator's
+    order shows."""
+    b, _ = linear_wave_box(32, 0, wave, amp=1e-3)
+    ratio = {}
+    for integ in ("rk2", "rk3"):
+        cfg = O.Config(b.nx, b.ny, b.nz, b.dx, b.dy, b.dz, G, 0.4, (0, 0, 0), integrator=integ)
+        dt0 = 0.8 * O.cfl_dt(cfg, b.cell, b.face)
+        sols = {m: O.step_dts(cfg, b.cell, b.face, [dt0 / m] * (4 * m)) for m in (1, 2, 32)}
+        ref = sols[32]
+
+        def err(m):
+            c, f = sols[m]
+            return np.abs(c - ref[0]).sum() + sum(np.abs(f[d] - ref[1][d]).sum() for d in range(3))
+
+        ratio[integ] = err(1) / err(2)
+    assert 3.0 < ratio["rk2"] < 5.5, ratio
+    assert ratio["rk3"] > 6.0, ratio
