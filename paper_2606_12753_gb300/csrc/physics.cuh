@@ -31,15 +31,39 @@ template <typename R> __host__ __device__ __forceinline__ R rmax(R a, R b) { ret
 __host__ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
 __host__ __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 
-// MC-limited slope of the middle of three values.
+// Sign-bit helpers (integer operations: they keep the sign tests of the
+// limiter off the FP64 pipe).
+__host__ __device__ __forceinline__ bool opposite_signs(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return (__double2hiint(a) ^ __double2hiint(b)) < 0;
+#else
+  return (a < 0.0) != (b < 0.0) && a != 0.0 && b != 0.0;
+#endif
+}
+__host__ __device__ __forceinline__ bool opposite_signs(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return (__float_as_int(a) ^ __float_as_int(b)) < 0;
+#else
+  return (a < 0.0f) != (b < 0.0f) && a != 0.0f && b != 0.0f;
+#endif
+}
+__host__ __device__ __forceinline__ double copysign_(double m, double s) { return copysign(m, s); }
+__host__ __device__ __forceinline__ float copysign_(float m, float s) { return copysignf(m, s); }
+__host__ __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
+__host__ __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
+
+// MC-limited slope of the middle of three values: with dm = q0 - qm and
+// dp = qp - q0, sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2) when dm and dp have the
+// same sign, else 0.  Doubling is exact, so 2 min(|dm|, |dp|) is the same
+// value as min(2|dm|, 2|dp|); a zero difference makes the minimum zero, so
+// only opposite signs need a test (which differs from testing dm dp > 0 only
+// when that product would underflow).
 template <typename R>
 __host__ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
   R dm = q0 - qm, dp = qp - q0;
-  // min(2|dm|, 2|dp|, |dm+dp|/2): doubling is exact, so 2 min(|dm|, |dp|)
-  // is the same value with one multiply fewer
-  R m = rmin(R(2) * rmin(rabs(dm), rabs(dp)), R(0.5) * rabs(dm + dp));
-  R s = dp > R(0) ? m : -m;
-  return dm * dp > R(0) ? s : R(0);
+  R m = fmin_(R(2) * fmin_(rabs(dm), rabs(dp)), R(0.5) * rabs(dm + dp));
+  m = opposite_signs(dm, dp) ? R(0) : m;
+  return copysign_(m, dp);
 }
 
 // Fast magnetosonic speed along the normal; w = (rho, vn, vt1, vt2, p, Bt1,
