@@ -35,6 +35,12 @@ UNIT = "Mcell-updates/s"
 # primitives W (11 arrays) and U^n (8), writes K1 (8) and W(U*); stage 2 reads
 # W(U*), U^n and K1, writes U^{n+1} and W(U^{n+1})
 STAGE_BYTES = {"fp64": (304, 368), "mixed": (184, 248), "fp32": (152, 184)}
+# SSP-RK3 stages: read W(U_in), U_in (and U^n in stages 2, 3), write U_out, W(U_out)
+STAGE_BYTES_RK3 = {"fp64": (304, 368, 368), "mixed": (216, 280, 280), "fp32": (152, 184, 184)}
+# the paper's own run of this workload (FP64, RK3, 3D OT 352^3, 10 steps): context, not a target
+PAPER_OT352 = {"time_10_steps_s": 13.9, "hardware": "NVIDIA A100 64 GB (Leonardo), NVHPC 24.5 OpenACC, managed memory",
+               "note": "total time of 10 steps of the paper's 3D Orszag-Tang test (Sec. 4, its figure of total "
+                       "execution time); other hardware and a whole-application time: context only"}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -47,7 +53,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="turbulence256",
-                   choices=["turbulence256", "turbulence256_learned", "ot2d128", "ot3d512", "blast_batch64"])
+                   choices=["turbulence256", "turbulence256_learned", "ot2d128", "ot3d512", "ot3d352_rk3",
+                            "blast_batch64"])
     p.add_argument("--precision", default=None, choices=["mixed", "fp64", "fp32"])
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--tile", default="0,0,0")
@@ -201,6 +208,7 @@ def cpu_oracle_rate(seconds: float, n: int = 64):
 WORKLOADS = {
     "turbulence256": ("mixed", 256),
     "turbulence256_learned": ("mixed", 256),
+    "ot3d352_rk3": ("fp64", 352),
     "ot2d128": ("fp64", 128),
     "ot3d512": ("mixed", 512),
     "blast_batch64": ("fp32", 64),
@@ -217,7 +225,7 @@ def make_box(args):
     from paper_2606_12753_gb300 import inputs as I
     if args.workload == "ot2d128":
         return I.orszag_tang_2d(args.n)
-    if args.workload == "ot3d512":
+    if args.workload in ("ot3d512", "ot3d352_rk3"):
         return I.orszag_tang_3d(args.n, seed=12753)
     return I.turbulence_3d(args.n, seed=2606)
 
@@ -232,6 +240,8 @@ def workload_config(args):
         "ot2d128": f"orszag_tang_2d_{args.n}: 2D Orszag-Tang {args.n}^2 periodic, PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
         "ot3d512": f"orszag_tang_3d_{args.n}: 3D Orszag-Tang {args.n}^3 periodic (+1% velocity noise), "
                    f"PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
+        "ot3d352_rk3": f"orszag_tang_3d_{args.n}_rk3: 3D Orszag-Tang {args.n}^3 periodic (+1% velocity noise), "
+                       f"PLM-MC+HLLD+upwind CT+SSP-RK3 (the paper's integrator and 3D OT size), CFL 0.4",
         "blast_batch64": f"blast_batch_{args.n}: {args.n} outflow MHD blast boxes, 32-128 cells per axis "
                          f"log-uniform, one persistent launch per call, autotuned tile, per-box CFL 0.4",
     }[args.workload]
@@ -281,6 +291,8 @@ def run_ours(args):
     tile = tuple(int(x) for x in args.tile.split(","))
     box = make_box(args)
     learned = args.workload == "turbulence256_learned"
+    rk3 = args.workload == "ot3d352_rk3"
+    stage_bytes = (STAGE_BYTES_RK3 if rk3 else STAGE_BYTES)[args.precision]
     switch_rep = None
     if learned:
         # training (not timed): faces of FP64 turbulence runs with seed 5,
@@ -290,7 +302,7 @@ def run_ours(args):
                                              batch=16384)
     stream = torch.cuda.Stream()
     solver = mhd.Solver(box, precision=args.precision, riemann="learned" if learned else "hlld", tile=tile,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, integrator="rk3" if rk3 else "rk2")
     if learned:
         solver.set_switch(sw.block.data_ptr(), tau)
     solver.set_state(box.cell, box.face)
@@ -330,11 +342,13 @@ def run_ours(args):
     value = world * box.ncell * args.steps / (ms_total / 1e3) / 1e6
 
     peak, peak_kind = peaks()
-    k = 0 if stage_ms[0] >= stage_ms[1] else 1
+    nst = len(stage_bytes)
+    k = max(range(nst), key=lambda i: stage_ms[i] / max(launches[i], 1))
     per_launch_ms = stage_ms[k] / max(launches[k], 1)
-    alg_bytes = STAGE_BYTES[args.precision][k] * box.ncell
+    alg_bytes = stage_bytes[k] * box.ncell
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    tag = f"stage_kernel{'_learned' if learned else ''}<{args.precision},{k + 1}>@{box.name}"
+    kname = "stage_kernel" + ("_learned" if learned else "") + ("_rk3" if rk3 else "")
+    tag = f"{kname}<{args.precision},{k + 1}>@{box.name}"
     traffic, src = traffic_from_profiles(tag)
     elem = 4 if args.precision == "fp32" else 8
     kelem = 8 if args.precision == "fp64" else 4
@@ -352,10 +366,14 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": tag, "peak_kind": peak_kind,
-                     "step_frac": value * 1e6 / world * sum(STAGE_BYTES[args.precision]) / 1e9 / peak},
-        "stage_ms_per_launch": [stage_ms[0] / max(launches[0], 1), stage_ms[1] / max(launches[1], 1)],
-        "gpu_launches": 2 * args.steps,
+                     "step_frac": value * 1e6 / world * sum(stage_bytes) / 1e9 / peak},
+        "stage_ms_per_launch": [stage_ms[i] / max(launches[i], 1) for i in range(nst)],
+        "gpu_launches": nst * args.steps,
     }
+    if rk3:
+        out["config"]["integrator"] = "SSP-RK3 (3 stage launches per step)"
+        out["time_10_steps_s"] = 10 * ms_total / args.steps / 1e3
+        out["paper_context"] = PAPER_OT352
     if learned:
         nh = st["faces_hll"] - st_w["faces_hll"]
         nd = st["faces_hlld"] - st_w["faces_hlld"]
@@ -387,7 +405,7 @@ def run_ours(args):
         # plain FP64 path on the same GPU and the L1 error of this path against it
         cmp = {}
         dt = solver.cfl_dt()
-        ref = mhd.Solver(box, precision="fp64", stream=stream.cuda_stream)
+        ref = mhd.Solver(box, precision="fp64", stream=stream.cuda_stream, integrator="rk3" if rk3 else "rk2")
         ref.set_state(box.cell, box.face)
         ref.step(dt, 1)
         ref.set_state(box.cell, box.face)
@@ -412,7 +430,8 @@ def run_ours(args):
             l1[names[5 + d]] = float(np.abs(f[d] - rf[d]).sum() / max(np.abs(rf[d]).sum(), 1e-3 * bnorm))
         cmp = {"fp64_value": box.ncell / (fp64_ms / 1e3) / 1e6, "unit": UNIT, "fp64_ms_per_step": fp64_ms,
                "steps": args.compare_steps, "dt": dt, "l1_rel_vs_fp64": l1,
-               "note": "FP64 GPU path (parity with the FP64 oracle at 1e-12) as the reference"}
+               "note": "FP64 GPU path with the same integrator (parity with the FP64 oracle at 1e-12) as the "
+                       "reference"}
         if learned:
             # the method without the switch (HLLD on every face) and HLL on
             # every face, same precision, same dt, same steps

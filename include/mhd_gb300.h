@@ -70,6 +70,10 @@ extern "C" {
 #define MHD_HLL 1
 #define MHD_LEARNED 2 /* per face: MLP predicts whether HLL suffices, else HLLD */
 
+#define MHD_RK2 0 /* two-stage Heun (default) */
+#define MHD_RK3 1 /* three-stage SSP Runge-Kutta of Shu & Osher (1988), the paper's default (Sec. 2.2);
+                     16x8 tile, single boxes, HLLD or HLL */
+
 #define MHD_EMF_UPWIND 0 /* Gardiner & Stone (2005) upwind contact average */
 #define MHD_EMF_MEAN 1   /* arithmetic mean of the four face EMFs (debug) */
 
@@ -85,6 +89,7 @@ typedef struct {
   double rho_floor;        /* density floor used in primitive recovery (1e-10) */
   double p_floor;          /* pressure floor (1e-10) */
   int tile_x, tile_y, tile_z; /* tile of the fused stage kernel; 0 = default */
+  int integrator;          /* MHD_RK2 | MHD_RK3 */
 } mhd_config;
 
 typedef struct {
@@ -130,11 +135,11 @@ int mhd_step_async(mhd_handle* h, double dt, int nsteps);
 
 /* Profiling: on = 1 records CUDA events on the handle's stream around every
  * stage-kernel launch, on = 0 stops.  mhd_get_profile synchronises and
- * returns, per stage kernel (index 0: stage 1, 1: stage 2), the summed device
- * time in ms and the number of launches recorded since the previous
- * mhd_get_profile, then clears the record. */
+ * returns, per stage kernel (index s: RK stage s+1; index 2 stays 0 for
+ * RK2), the summed device time in ms and the number of launches recorded
+ * since the previous mhd_get_profile, then clears the record. */
 int mhd_set_profiling(mhd_handle* h, int on);
-int mhd_get_profile(mhd_handle* h, double ms[2], long long launches[2]);
+int mhd_get_profile(mhd_handle* h, double ms[3], long long launches[3]);
 
 /* Evaluate the spatial operator L(U) of the current state (one stage-1 pass:
  * reconstruction, Riemann fluxes, flux divergence, edge EMFs, -curl E) and

@@ -26,6 +26,12 @@ size_t smem_bytes_fp32(int, int);
 cudaError_t launch_stage_learned_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_stage_learned_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_stage_learned_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_rk3_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_rk3_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_rk3_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t set_smem_rk3_fp64(size_t);
+cudaError_t set_smem_rk3_mixed(size_t);
+cudaError_t set_smem_rk3_fp32(size_t);
 cudaError_t set_smem_learned_fp64(size_t);
 cudaError_t set_smem_learned_mixed(size_t);
 cudaError_t set_smem_learned_fp32(size_t);
@@ -35,6 +41,13 @@ cudaError_t launch_prims_fp32(unsigned, cudaStream_t, const Geo&, const StageArg
 
 cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nb, size_t smem, cudaStream_t st,
                          const Geo& g, const StageArgs& a) {
+  if (stage >= ST_RK3_1) {
+    switch (prec) {
+      case P_FP64: return launch_stage_rk3_fp64(stage, nb, smem, st, g, a);
+      case P_MIXED: return launch_stage_rk3_mixed(stage, nb, smem, st, g, a);
+      default: return launch_stage_rk3_fp32(stage, nb, smem, st, g, a);
+    }
+  }
   if (g.riemann == 2) {
     // learned switch: needs the network; 16 x 8 tile only
     if (!a.mlp) return cudaErrorInvalidValue;
@@ -55,6 +68,13 @@ cudaError_t launch_prims(int prec, unsigned nb, cudaStream_t st, const Geo& g, c
     case P_FP64: return launch_prims_fp64(nb, st, g, a);
     case P_MIXED: return launch_prims_mixed(nb, st, g, a);
     default: return launch_prims_fp32(nb, st, g, a);
+  }
+}
+cudaError_t stage_set_smem_rk3(int prec, size_t bytes) {
+  switch (prec) {
+    case P_FP64: return set_smem_rk3_fp64(bytes);
+    case P_MIXED: return set_smem_rk3_mixed(bytes);
+    default: return set_smem_rk3_fp32(bytes);
   }
 }
 cudaError_t stage_set_smem_learned(int prec, size_t bytes) {
@@ -93,6 +113,7 @@ struct mhd_handle {
   size_t welem = 8;         // bytes per primitive element
   void* U[2] = {nullptr, nullptr};
   void* K1 = nullptr;
+  void* Urk[2] = {nullptr, nullptr};        // RK3: the intermediate states U1, U2
   void* W[2] = {nullptr, nullptr};
   unsigned long long* words = nullptr;     // [0,1] CFL words (step parity), [2] reductions, [3] status,
                                            // [4] scratch, [8..] counters
@@ -186,6 +207,11 @@ static int validate(const mhd_config* c, mhd_handle* h) {
     return fail(h, MHD_ERR_INVALID, "tile %dx%d is not instantiated for this precision", tx, ty);
   if (c->riemann == MHD_LEARNED && (tx != 16 || ty != 8))
     return fail(h, MHD_ERR_INVALID, "the learned switch is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
+  if (c->integrator != MHD_RK2 && c->integrator != MHD_RK3) return fail(h, MHD_ERR_INVALID, "unknown integrator");
+  if (c->integrator == MHD_RK3 && (tx != 16 || ty != 8))
+    return fail(h, MHD_ERR_INVALID, "SSP-RK3 is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
+  if (c->integrator == MHD_RK3 && c->riemann == MHD_LEARNED)
+    return fail(h, MHD_ERR_INVALID, "the learned switch runs with the RK2 integrator");
   if (stage_smem_bytes(c->precision, tx, ty) > 227 * 1024)
     return fail(h, MHD_ERR_INVALID, "tile %dx%d needs %zu B of shared memory (> 227 KB)", tx, ty,
                 stage_smem_bytes(c->precision, tx, ty));
@@ -246,6 +272,8 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   if (e == cudaSuccess) e = cudaMalloc(&h->U[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->U[1], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->K1, kbytes);
+  if (e == cudaSuccess && cfg->integrator == MHD_RK3) e = cudaMalloc(&h->Urk[0], bytes);
+  if (e == cudaSuccess && cfg->integrator == MHD_RK3) e = cudaMalloc(&h->Urk[1], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->W[0], wbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->W[1], wbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->words, 64 * sizeof(unsigned long long));
@@ -265,6 +293,7 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   if (e == cudaSuccess) e = cudaMemsetAsync(h->K1, 0, kbytes, h->stream);
   if (e == cudaSuccess) e = stage_set_smem(cfg->precision, h->geo.TX, h->geo.TY, h->smem_bytes);
   if (e == cudaSuccess && cfg->riemann == MHD_LEARNED) e = stage_set_smem_learned(cfg->precision, h->smem_bytes);
+  if (e == cudaSuccess && cfg->integrator == MHD_RK3) e = stage_set_smem_rk3(cfg->precision, h->smem_bytes);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     fail(nullptr, MHD_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
@@ -282,6 +311,8 @@ extern "C" void mhd_destroy(mhd_handle* h) {
   cudaFree(h->U[0]);
   cudaFree(h->U[1]);
   cudaFree(h->K1);
+  cudaFree(h->Urk[0]);
+  cudaFree(h->Urk[1]);
   cudaFree(h->W[0]);
   cudaFree(h->W[1]);
   cudaFree(h->words);
@@ -367,12 +398,45 @@ static cudaError_t ensure_prims(mhd_handle* h) {
   return cudaSuccess;
 }
 
+// One SSP-RK3 step: three stage launches, U^n -> U1 -> U2 -> U^{n+1}.  The
+// primitives alternate W[cur] -> W[cur^1] -> W[cur] -> W[cur^1], so W[cur^1]
+// holds those of U^{n+1} when cur flips.
+static cudaError_t launch_step_rk3(mhd_handle* h, double dt) {
+  const Geo& g = h->geo;
+  const unsigned nblocks = (unsigned)(g.ntx * g.nty * g.nchunk);
+  const int prec = h->cfg.precision;
+  StageArgs a = base_args(h);
+  a.dt = dt;
+  a.dtword = h->words + h->parity;
+  a.nextword = h->words + (h->parity ^ 1);
+  a.U = h->U[h->cur];
+  void* in[3] = {h->U[h->cur], h->Urk[0], h->Urk[1]};
+  void* outs[3] = {h->Urk[0], h->Urk[1], h->U[h->cur ^ 1]};
+  void* win[3] = {h->W[h->cur], h->W[h->cur ^ 1], h->W[h->cur]};
+  void* wout[3] = {h->W[h->cur ^ 1], h->W[h->cur], h->W[h->cur ^ 1]};
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < 3; ++s) {
+    a.Uin = in[s];
+    a.Uout = outs[s];
+    a.Win = win[s];
+    a.Wout = wout[s];
+    if (h->profiling && (e = record_event(h))) return e;
+    e = launch_stage(prec, ST_RK3_1 + s, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a);
+    if (e) return e;
+  }
+  if (h->profiling && (e = record_event(h))) return e;
+  h->cur ^= 1;
+  h->parity ^= 1;
+  return cudaSuccess;
+}
+
 static cudaError_t launch_step(mhd_handle* h, double dt) {
   const Geo& g = h->geo;
   const unsigned nblocks = (unsigned)(g.ntx * g.nty * g.nchunk);
   const int prec = h->cfg.precision;
   cudaError_t e = ensure_prims(h);
   if (e) return e;
+  if (h->cfg.integrator == MHD_RK3) return launch_step_rk3(h, dt);
   StageArgs a = base_args(h);
   a.dt = dt;
   a.dtword = h->words + h->parity;
@@ -493,20 +557,22 @@ extern "C" int mhd_set_profiling(mhd_handle* h, int on) {
   return MHD_OK;
 }
 
-extern "C" int mhd_get_profile(mhd_handle* h, double ms[2], long long launches[2]) {
+extern "C" int mhd_get_profile(mhd_handle* h, double ms[3], long long launches[3]) {
   if (!h) return MHD_ERR_INVALID;
   if (!ms || !launches) return fail(h, MHD_ERR_INVALID, "null output pointer");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  ms[0] = ms[1] = 0.0;
-  launches[0] = launches[1] = 0;
-  for (size_t i = 0; i + 3 <= h->ev_used; i += 3) {
-    float a = 0.f, b = 0.f;
-    CUDA_TRY(h, cudaEventElapsedTime(&a, h->ev_pool[i], h->ev_pool[i + 1]));
-    CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev_pool[i + 1], h->ev_pool[i + 2]));
-    ms[0] += a;
-    ms[1] += b;
-    launches[0]++;
-    launches[1]++;
+  const size_t nst = h->cfg.integrator == MHD_RK3 ? 3 : 2;   // events per step: nst + 1
+  for (int s = 0; s < 3; ++s) {
+    ms[s] = 0.0;
+    launches[s] = 0;
+  }
+  for (size_t i = 0; i + nst + 1 <= h->ev_used; i += nst + 1) {
+    for (size_t s = 0; s < nst; ++s) {
+      float t = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&t, h->ev_pool[i + s], h->ev_pool[i + s + 1]));
+      ms[s] += t;
+      launches[s]++;
+    }
   }
   h->ev_used = 0;
   return MHD_OK;
@@ -777,6 +843,8 @@ extern "C" int mhd_batch_create(int nbox, const mhd_config* cfgs, void* cuda_str
       return bfail(nullptr, MHD_ERR_INVALID, "all boxes of a batch share precision, Riemann solver and EMF mode");
     if (cfgs[i].riemann == MHD_LEARNED)
       return bfail(nullptr, MHD_ERR_INVALID, "batches solve with HLLD or HLL; the learned switch is single-box only");
+    if (cfgs[i].integrator != MHD_RK2)
+      return bfail(nullptr, MHD_ERR_INVALID, "batches step with the RK2 integrator; SSP-RK3 is single-box only");
   }
   mhd_batch* b = new (std::nothrow) mhd_batch();
   if (!b) return bfail(nullptr, MHD_ERR_NOMEM, "host allocation failed");

@@ -53,11 +53,20 @@ struct Geo {
   long long total;         // packed state length (5 ncell + faces)
 };
 
+// Stage ids: RK2 (Heun) stages 1, 2; SSP-RK3 (Shu-Osher) stages 3, 4, 5.
+enum { ST_RK2_1 = 1, ST_RK2_2 = 2, ST_RK3_1 = 3, ST_RK3_2 = 4, ST_RK3_3 = 5 };
+template <int STAGE> struct StageTraits {
+  static constexpr bool rk3 = STAGE >= ST_RK3_1;
+  static constexpr bool first = STAGE == ST_RK2_1 || STAGE == ST_RK3_1;   // clears the next step's CFL word
+  static constexpr bool last = STAGE == ST_RK2_2 || STAGE == ST_RK3_3;    // produces U^{n+1} and its CFL max
+};
+
 struct StageArgs {
   const void* U;       // U^n (type S)
+  const void* Uin;     // RK3: the stage's input state (U^n, U1 or U2; type S)
   const void* K1;      // stage-1 increments (type K): written by stage 1, read by stage 2
   void* K1out;         // stage 1: where L(U^n) goes
-  void* Uout;          // stage 2: U^{n+1}
+  void* Uout;          // RK2 stage 2: U^{n+1}; RK3: the stage's output state (U1, U2 or U^{n+1})
   const void* Win;     // primitives of the stage's input state (type R)
   void* Wout;          // primitives of the stage's output state
   unsigned long long* dtword;   // CFL max of the step's starting state (bits of a double)

@@ -66,4 +66,27 @@ cudaError_t set_smem_learned_fp64(size_t bytes) {
   return e;
 }
 
+// SSP-RK3 stages (ids 3, 4, 5) are instantiated for the 16 x 8 tile only.
+cudaError_t launch_stage_rk3_fp64(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
+                                const StageArgs& args) {
+  if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
+  if (stage == ST_RK3_1) stage_kernel<P_FP64, ST_RK3_1, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  else if (stage == ST_RK3_2) stage_kernel<P_FP64, ST_RK3_2, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  else if (stage == ST_RK3_3) stage_kernel<P_FP64, ST_RK3_3, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t set_smem_rk3_fp64(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<P_FP64, ST_RK3_1, 16, 8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage_kernel<P_FP64, ST_RK3_2, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage_kernel<P_FP64, ST_RK3_3, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  return e;
+}
+
 }  // namespace mhd

@@ -82,6 +82,7 @@ template <int PREC, int STAGE>
 __device__ __forceinline__ double cons_at(const StageArgs& a, long long idx, double dt) {
   using S = typename Prec<PREC>::S;
   using K = typename Prec<PREC>::K;
+  if (StageTraits<STAGE>::rk3) return (double)((const S*)a.Uin)[idx];   // stored input state
   if (PREC == P_FP32) {
     float u = (float)((const S*)a.U)[idx];
     if (STAGE == 2) u = u + (float)dt * (float)((const K*)a.K1)[idx];
@@ -430,8 +431,25 @@ struct StageKernel {
   }
 
   // new value of one conserved quantity from its increment l:
-  // stage 1 U* = U^n + dt K1 (K1 = l rounded to K), stage 2 U^n + dt/2 (K1 + l)
+  // RK2 stage 1 U* = U^n + dt K1 (K1 = l rounded to K), stage 2 U^n + dt/2 (K1 + l);
+  // RK3 (input state U_in): U1 = U_in + dt l, U2 = 3/4 U^n + 1/4 (U_in + dt l),
+  // U^{n+1} = 1/3 U^n + 2/3 (U_in + dt l)
   static __device__ __forceinline__ S advance(const StageArgs& a, long long gidx, R l, double dt) {
+    if (StageTraits<STAGE>::rk3) {
+      const S ui = ((const S*)a.Uin)[gidx];
+      if (PREC == P_FP32) {
+        const float e = ui + (float)dt * l;
+        if (STAGE == ST_RK3_1) return e;
+        const float un = ((const S*)a.U)[gidx];
+        if (STAGE == ST_RK3_2) return 0.75f * un + 0.25f * e;
+        return un / 3.0f + 2.0f / 3.0f * e;
+      }
+      const double e = fma(dt, (double)l, (double)ui);
+      if (STAGE == ST_RK3_1) return (S)e;
+      const double un = (double)((const S*)a.U)[gidx];
+      if (STAGE == ST_RK3_2) return (S)(0.75 * un + 0.25 * e);
+      return (S)(un / 3.0 + 2.0 / 3.0 * e);
+    }
     const S un = ((const S*)a.U)[gidx];
     if (STAGE == 1) {
       const K k1 = (K)l;
@@ -446,7 +464,7 @@ struct StageKernel {
   }
 
   static __device__ __forceinline__ void emit(const StageArgs& a, long long gidx, R l, S v) {
-    if (STAGE == 1) ((K*)a.K1out)[gidx] = (K)l;
+    if (STAGE == ST_RK2_1) ((K*)a.K1out)[gidx] = (K)l;
     else ((S*)a.Uout)[gidx] = v;
   }
 
@@ -553,7 +571,7 @@ struct StageKernel {
       if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
 #pragma unroll
       for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
-      if (STAGE == 2) {
+      if (StageTraits<STAGE>::last) {
         const R sp = cfl_speed<R>(g, w);
         smax = sp > smax ? sp : smax;
       }
@@ -586,7 +604,7 @@ struct StageKernel {
     const int kb = chunk * g.TZ;
     const int ke = min(kb + g.TZ, g.n[2]);
 
-    if (STAGE == 1 && item == 0 && threadIdx.x == 0) *a.nextword = 0ull;
+    if (StageTraits<STAGE>::first && item == 0 && threadIdx.x == 0) *a.nextword = 0ull;
     double dt = a.dt;
     if (!(dt > 0.0)) {
       const double m = __longlong_as_double((long long)*a.dtword);
@@ -645,7 +663,7 @@ struct StageKernel {
       if (nrho) atomicAdd(&a.counters[C_RHO_FLOOR], (unsigned long long)nrho);
       if (np) atomicAdd(&a.counters[C_P_FLOOR], (unsigned long long)np);
       if (anybad) atomicOr(a.status, (unsigned)ST_NONFINITE);
-      if (STAGE == 2 && sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
+      if (StageTraits<STAGE>::last && sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
     }
   }
 };

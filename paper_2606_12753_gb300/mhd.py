@@ -22,6 +22,8 @@ MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
 MHD_FP64, MHD_MIXED, MHD_FP32 = 0, 1, 2
 MHD_HLLD, MHD_HLL, MHD_LEARNED = 0, 1, 2
 MHD_EMF_UPWIND, MHD_EMF_MEAN = 0, 1
+MHD_RK2, MHD_RK3 = 0, 1
+INTEGRATORS = {"rk2": MHD_RK2, "rk3": MHD_RK3}
 
 PRECISIONS = {"fp64": MHD_FP64, "mixed": MHD_MIXED, "fp32": MHD_FP32}
 RIEMANN = {"hlld": MHD_HLLD, "hll": MHD_HLL, "learned": MHD_LEARNED}
@@ -34,7 +36,8 @@ class mhd_config(C.Structure):
                 ("bc", C.c_int * 3),
                 ("precision", C.c_int), ("riemann", C.c_int), ("emf", C.c_int),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
-                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int)]
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
+                ("integrator", C.c_int)]
 
 
 class mhd_stats(C.Structure):
@@ -201,10 +204,12 @@ def mhd_set_profiling(h, on: bool):
 
 
 def mhd_get_profile(h):
-    ms = (C.c_double * 2)()
-    n = (C.c_longlong * 2)()
+    """(ms per stage kernel, launches per stage kernel): 3 entries, the third
+    used by RK3 only."""
+    ms = (C.c_double * 3)()
+    n = (C.c_longlong * 3)()
     _check(h, load().mhd_get_profile(h, ms, n))
-    return [ms[0], ms[1]], [n[0], n[1]]
+    return [ms[0], ms[1], ms[2]], [n[0], n[1], n[2]]
 
 
 def mhd_cfl_dt(h) -> float:
@@ -252,7 +257,7 @@ class Solver:
     bc, gamma (and optionally cfl) -- e.g. ``inputs.Box``."""
 
     def __init__(self, box, precision="fp64", riemann="hlld", emf="upwind", tile=(0, 0, 0),
-                 stream=None, cfl=None, rho_floor=1e-10, p_floor=1e-10):
+                 stream=None, cfl=None, rho_floor=1e-10, p_floor=1e-10, integrator="rk2"):
         c = mhd_default_config(box.nx, box.ny, box.nz)
         c.dx, c.dy, c.dz = box.dx, box.dy, box.dz
         c.gamma = box.gamma
@@ -263,6 +268,7 @@ class Solver:
         c.emf = MHD_EMF_MEAN if emf == "mean" else MHD_EMF_UPWIND
         c.rho_floor, c.p_floor = rho_floor, p_floor
         c.tile_x, c.tile_y, c.tile_z = tile
+        c.integrator = INTEGRATORS[integrator] if isinstance(integrator, str) else integrator
         self.cfg = c
         self.dims = (box.nx, box.ny, box.nz)
         self.bc = tuple(box.bc)

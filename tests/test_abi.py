@@ -84,3 +84,31 @@ def test_batch_rejects_the_learned_switch():
     with pytest.raises(mhd.MHDError) as ei:
         mhd.Batch(boxes, precision="fp32", riemann="learned")
     assert "learned" in str(ei.value)
+
+
+def test_rk3_validation():
+    from paper_2606_12753_gb300 import inputs as I
+    c = mhd.mhd_default_config(32, 32, 32)
+    assert c.integrator == mhd.MHD_RK2
+    c.integrator = mhd.MHD_RK3
+    c.tile_x, c.tile_y = 8, 8
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert "16x8" in str(ei.value)
+    c.tile_x, c.tile_y = 0, 0
+    c.riemann = mhd.MHD_LEARNED
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert "RK2" in str(ei.value)
+    c.integrator = 7
+    c.riemann = mhd.MHD_HLLD
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_create(c)
+    assert "integrator" in str(ei.value)
+    boxes = [I.uniform_state((16, 16, 16)), I.uniform_state((8, 16, 16))]
+    cfgs = (mhd.mhd_config * 2)(*[mhd.box_config(b, "fp32") for b in boxes])
+    for k in range(2):
+        cfgs[k].integrator = mhd.MHD_RK3
+    h = mhd.C.c_void_p()
+    rc = mhd.load().mhd_batch_create(2, cfgs, None, mhd.C.byref(h))
+    assert rc == mhd.MHD_ERR_INVALID

@@ -180,3 +180,35 @@ def test_learned_operator_at_256_sampled(smooth):
         got_f.append([gf[0][k, j, i], gf[1][k, j, i], gf[2][k, j, i]])
     _compare(np.array(got_c), np.array(ref_c), np.array(got_f), np.array(ref_f), _operator_tol("mixed"),
              "learned L(U)")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_rk3_step_at_352_sampled(precision):
+    """SSP-RK3 on the 3D Orszag-Tang start at 352^3 (the paper's size for its
+    own 3D OT run): one step, sampled cells against the oracle's RK3 step on
+    sub-boxes of radius 7 (the RK3 step is local to 6 cells)."""
+    from paper_2606_12753_gb300 import mhd
+    n = 352
+    start = I.orszag_tang_3d(n, seed=12753)
+    s = mhd.Solver(start, precision=precision, integrator="rk3")
+    s.set_state(start.cell, start.face)
+    dt = s.cfl_dt()
+    s.step(dt, 1)
+    c, f = s.get_state()
+    s.close()
+    rng = np.random.default_rng(352)
+    pts = [(0, 0, 0), (15, 7, 31), (16, 8, 32), (351, 351, 351), (175, 176, 200)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(10)]
+    got_c, ref_c, got_f, ref_f = [], [], [], []
+    h = 7
+    for (i, j, k) in pts:
+        cfg, cell, face = subbox(start.cell, start.face, (n, n, n), (i, j, k), h, (start.dx, start.dy, start.dz),
+                                 start.gamma)
+        cfg.integrator = "rk3"
+        rc, rf = O.step_dts(cfg, cell, face, [dt])
+        ref_c.append(rc[:, h, h, h])
+        got_c.append(c[:, k, j, i])
+        ref_f.append([rf[0][h, h, h], rf[1][h, h, h], rf[2][h, h, h]])
+        got_f.append([f[0][k, j, i], f[1][k, j, i], f[2][k, j, i]])
+    _compare(np.array(got_c), np.array(ref_c), np.array(got_f), np.array(ref_f), TOL[precision],
+             f"rk3 step {precision}", state=True)

@@ -49,3 +49,19 @@ def test_step_is_local_to_radius_4():
         for h in (4, 7):
             assert _matches(b, step, rc, rf, c, h), (c, h)
     assert not all(_matches(b, step, rc, rf, c, 3) for c in cs)
+
+
+def test_rk3_step_is_local_to_radius_6():
+    b = _box()
+    cfg = ocfg(b, integrator="rk3")
+    dt = O.cfl_dt(cfg, b.cell, b.face)
+    rc, rf = O.step_dts(cfg, b.cell, b.face, [dt])
+
+    def step(cfg_s, c, f):
+        cfg_s.integrator = "rk3"
+        return O.step_dts(cfg_s, c, f, [dt])
+
+    cs = _centres(b, n=3)
+    for c in cs:
+        assert _matches(b, step, rc, rf, c, 6), c
+    assert not all(_matches(b, step, rc, rf, c, 5) for c in cs)
