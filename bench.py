@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="turbulence256",
                    choices=["turbulence256", "turbulence256_learned", "ot2d128", "ot3d512", "ot3d352_rk3",
-                            "blast_batch64"])
+                            "riemann2d3200_hll", "blast_batch64"])
     p.add_argument("--precision", default=None, choices=["mixed", "fp64", "fp32"])
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--tile", default="0,0,0")
@@ -209,6 +209,7 @@ WORKLOADS = {
     "turbulence256": ("mixed", 256),
     "turbulence256_learned": ("mixed", 256),
     "ot3d352_rk3": ("fp64", 352),
+    "riemann2d3200_hll": ("fp64", 3200),
     "ot2d128": ("fp64", 128),
     "ot3d512": ("mixed", 512),
     "blast_batch64": ("fp32", 64),
@@ -227,6 +228,8 @@ def make_box(args):
         return I.orszag_tang_2d(args.n)
     if args.workload in ("ot3d512", "ot3d352_rk3"):
         return I.orszag_tang_3d(args.n, seed=12753)
+    if args.workload == "riemann2d3200_hll":
+        return I.riemann_2d(args.n, seed=3200)
     return I.turbulence_3d(args.n, seed=2606)
 
 
@@ -242,6 +245,9 @@ def workload_config(args):
                    f"PLM-MC+HLLD+upwind CT+RK2, CFL 0.4",
         "ot3d352_rk3": f"orszag_tang_3d_{args.n}_rk3: 3D Orszag-Tang {args.n}^3 periodic (+1% velocity noise), "
                        f"PLM-MC+HLLD+upwind CT+SSP-RK3 (the paper's integrator and 3D OT size), CFL 0.4",
+        "riemann2d3200_hll": f"riemann2d_{args.n}: seeded four-quadrant 2D MHD Riemann problem {args.n}^2 x 1, "
+                             f"outflow, PLM-MC+HLL+upwind CT+RK2, CFL 0.4 (stand-in for the paper's 2D Riemann "
+                             f"test, whose quadrant states it does not print)",
         "blast_batch64": f"blast_batch_{args.n}: {args.n} outflow MHD blast boxes, 32-128 cells per axis "
                          f"log-uniform, one persistent launch per call, autotuned tile, per-box CFL 0.4",
     }[args.workload]
@@ -301,7 +307,8 @@ def run_ours(args):
         sw, tau, switch_rep = T.train_switch(n=args.n, nfaces=args.switch_faces, seed=5, steps=args.switch_steps,
                                              batch=16384)
     stream = torch.cuda.Stream()
-    solver = mhd.Solver(box, precision=args.precision, riemann="learned" if learned else "hlld", tile=tile,
+    riemann = "learned" if learned else ("hll" if args.workload == "riemann2d3200_hll" else "hlld")
+    solver = mhd.Solver(box, precision=args.precision, riemann=riemann, tile=tile,
                         stream=stream.cuda_stream, integrator="rk3" if rk3 else "rk2")
     if learned:
         solver.set_switch(sw.block.data_ptr(), tau)
@@ -405,7 +412,8 @@ def run_ours(args):
         # plain FP64 path on the same GPU and the L1 error of this path against it
         cmp = {}
         dt = solver.cfl_dt()
-        ref = mhd.Solver(box, precision="fp64", stream=stream.cuda_stream, integrator="rk3" if rk3 else "rk2")
+        ref = mhd.Solver(box, precision="fp64", riemann="hll" if riemann == "hll" else "hlld", stream=stream.cuda_stream,
+                         integrator="rk3" if rk3 else "rk2")
         ref.set_state(box.cell, box.face)
         ref.step(dt, 1)
         ref.set_state(box.cell, box.face)

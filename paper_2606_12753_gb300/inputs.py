@@ -246,6 +246,41 @@ def blast_box(dims, seed_rng: np.random.Generator, h: float = 1.0 / 128, radius:
                meta={"centre": centre, "ratio": ratio})
 
 
+def riemann_2d(n: int = 3200, seed: int = 3200, gamma: float = GAMMA) -> Box:
+    """Seeded four-quadrant 2D MHD Riemann problem on [0,1]^2 (n x n x 1,
+    outflow in x and y, periodic along the single z cell), quadrants split at
+    x = 1/2 and y = 1/2.  Each quadrant has its own rho in [0.5, 2], p in
+    [0.3, 1.5], v in [-0.5, 0.5]^2 x [-0.2, 0.2] and B_z in [-0.5, 0.5]; B_x
+    takes one of two values by the y-half and B_y one of two by the x-half
+    (|B| in [0.2, 0.8]), so the face field is divergence-free.  A stand-in of
+    the paper's 2D Riemann workload, whose quadrant states it does not print."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, 1)
+    h = 1.0 / n
+    bc = (OUTFLOW, OUTFLOW, PERIODIC)
+    q = {key: (rng.uniform(0.5, 2.0), rng.uniform(0.3, 1.5), rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5),
+               rng.uniform(-0.2, 0.2), rng.uniform(-0.5, 0.5)) for key in ("ll", "lr", "ul", "ur")}
+    sgn = lambda: 1.0 if rng.uniform() < 0.5 else -1.0  # noqa: E731
+    bx_half = (sgn() * rng.uniform(0.2, 0.8), sgn() * rng.uniform(0.2, 0.8))   # y < 1/2, y > 1/2
+    by_half = (sgn() * rng.uniform(0.2, 0.8), sgn() * rng.uniform(0.2, 0.8))   # x < 1/2, x > 1/2
+    xc = (np.arange(n) + 0.5) * h
+    upper = xc > 0.5                       # by the cell centre
+    X, Y = np.meshgrid(upper, upper, indexing="xy")   # X: x > 1/2, Y: y > 1/2, shape (ny, nx)
+    key = np.where(Y, np.where(X, "ur", "ul"), np.where(X, "lr", "ll"))
+    fields = np.zeros((6, n, n))
+    for name, vals in q.items():
+        m = key == name
+        for v in range(6):
+            fields[v][m] = vals[v]
+    rho, p, vx, vy, vz, bz = [f[None] for f in fields]
+    bx = np.where(upper, bx_half[1], bx_half[0])[None, :, None] * np.ones((1, n, n + 1))
+    by = np.where(upper, by_half[1], by_half[0])[None, None, :] * np.ones((1, n + 1, n))
+    face = [np.ascontiguousarray(bx), np.ascontiguousarray(by), np.ascontiguousarray(bz.copy())]
+    cell = conserved(rho, (vx, vy, vz), p, face, dims, bc, gamma)
+    return Box(n, n, 1, h, h, h, bc, gamma, cell, face, name=f"riemann2d_{n}",
+               meta={"quadrants": {k: [float(x) for x in v] for k, v in q.items()}, "bx": bx_half, "by": by_half})
+
+
 def blast_batch(nbox: int = 64, seed: int = 64, nmin: int = 32, nmax: int = 128,
                 size_scale: float = 1.0) -> list:
     """``nbox`` independent blast boxes; each axis length is log-uniform in

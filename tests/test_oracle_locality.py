@@ -65,3 +65,25 @@ def test_rk3_step_is_local_to_radius_6():
     for c in cs:
         assert _matches(b, step, rc, rf, c, 6), c
     assert not all(_matches(b, step, rc, rf, c, 5) for c in cs)
+
+
+def test_clamped_subbox_on_an_outflow_domain():
+    # 2D outflow domain: a sub-box clamped to the domain (its sides that meet
+    # the domain edge are the domain's boundary) reproduces the full step at
+    # its sample, near the edges and the corners too
+    b = I.riemann_2d(40, seed=9)
+    cfg = ocfg(b, riemann=O.HLL)
+    dt = O.cfl_dt(cfg, b.cell, b.face)
+    rc, rf = O.step_dts(cfg, b.cell, b.face, [dt])
+    n, h = b.nx, 7
+    for (i, j) in [(0, 0), (1, 38), (39, 39), (20, 19), (5, 33)]:
+        lx, hx, ly, hy = max(0, i - h), min(n, i + h + 1), max(0, j - h), min(n, j + h + 1)
+        sub = O.Config(hx - lx, hy - ly, 1, b.dx, b.dy, b.dz, b.gamma, 0.4, (O.OUTFLOW, O.OUTFLOW, O.PERIODIC),
+                       riemann=O.HLL)
+        c = np.ascontiguousarray(b.cell[:, :, ly:hy, lx:hx])
+        f = [np.ascontiguousarray(b.face[0][:, ly:hy, lx:hx + 1]), np.ascontiguousarray(b.face[1][:, ly:hy + 1, lx:hx]),
+             np.ascontiguousarray(b.face[2][:, ly:hy, lx:hx])]
+        sc, sf = O.step_dts(sub, c, f, [dt])
+        assert np.array_equal(sc[:, 0, j - ly, i - lx], rc[:, 0, j, i]), (i, j)
+        for d in range(3):
+            assert sf[d][0, j - ly, i - lx] == rf[d][0, j, i], (i, j, d)
