@@ -52,7 +52,7 @@ class _Cfg(C.Structure):
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("emf_mean", C.c_int), ("riemann", C.c_int),
                 ("mlp", C.POINTER(C.c_double)), ("mlp_zt", C.c_double),
-                ("choice", C.POINTER(C.c_ubyte))]
+                ("choice", C.POINTER(C.c_ubyte)), ("recon", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -84,6 +84,8 @@ class Config:
     choice: np.ndarray | None = None
     # time integrator of step / step_dts: "rk2" (Heun) or "rk3" (Shu-Osher SSP)
     integrator: str = "rk2"
+    # reconstruction: 0 = MC on the primitives, 1 = MC on the characteristic variables
+    recon: int = 0
 
     def c(self) -> _Cfg:
         mp = None
@@ -102,7 +104,7 @@ class Config:
             assert cp is not None, "MASK needs the per-face choices"
         return _Cfg(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.gamma, self.cfl,
                     (C.c_int * 3)(*self.bc), self.rho_floor, self.p_floor, self.emf_mean,
-                    self.riemann, mp, self.mlp_zt, cp)
+                    self.riemann, mp, self.mlp_zt, cp, self.recon)
 
     def face_shapes(self):
         o = [1 if b == OUTFLOW else 0 for b in self.bc]
@@ -147,6 +149,10 @@ def lib():
         L.orc_features.argtypes = [_P, _P, C.c_double, C.c_double, _P]
         L.orc_mlp_logit.restype = C.c_double
         L.orc_mlp_logit.argtypes = [_P, _P]
+        L.orc_char_eig.restype = None
+        L.orc_char_eig.argtypes = [_P, C.c_double, C.c_double, _P, _P, _P]
+        L.orc_char_slope.restype = None
+        L.orc_char_slope.argtypes = [_P, _P, _P, C.c_double, C.c_double, _P]
         L.orc_switch_logits.restype = None
         L.orc_switch_logits.argtypes = [C.POINTER(_Cfg), PP, PF, _P]
         _lib = L
@@ -292,6 +298,22 @@ def switch_logit(params, f) -> float:
     p = _vec(params, 1633)
     f = _vec(f, 16)
     return lib().orc_mlp_logit(_ptr(p), _ptr(f))
+
+
+def char_eig(w, bn: float, gamma: float):
+    """(eigenvalues (7,), R (7, 7) with eigenvectors as columns, L (7, 7) with
+    left eigenvectors as rows) of the primitive Jacobian, Roe-Balsara normalised."""
+    w = _vec(w, 7)
+    lam, R, L = np.zeros(7), np.zeros((7, 7)), np.zeros((7, 7))
+    lib().orc_char_eig(_ptr(w), bn, gamma, _ptr(lam), _ptr(R), _ptr(L))
+    return lam, R, L
+
+
+def char_slope(wm, w0, wp, bn0: float, gamma: float) -> np.ndarray:
+    wm, w0, wp = _vec(wm, 7), _vec(w0, 7), _vec(wp, 7)
+    out = np.zeros(7)
+    lib().orc_char_slope(_ptr(wm), _ptr(w0), _ptr(wp), bn0, gamma, _ptr(out))
+    return out
 
 
 def switch_logits(cfg: Config, cell, face) -> np.ndarray:

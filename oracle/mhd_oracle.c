@@ -68,6 +68,7 @@ typedef struct {
   const unsigned char *choice; /* ORC_MASK: 1 = HLLD, 0 = HLL for the lower face of interior
                                   cell s along d at [d * nx*ny*nz + s]; ghost faces take the
                                   choice of the cell they wrap to (periodic boxes) */
+  int recon;        /* 0: MC on the primitives; 1: MC on the characteristic variables */
 } orc_cfg;
 
 typedef struct {
@@ -326,6 +327,112 @@ double orc_mlp_logit(const double *prm, const double *f) {
   return z + b3[0];
 }
 
+/* ------------------------------------------------------------------------ */
+/* characteristic reconstruction (the paper's alternative, Sec. 2.2)         */
+/* ------------------------------------------------------------------------ */
+
+/* Eigenvalues lam[7], right eigenvectors (columns of R, row-major 7x7) and
+ * left eigenvectors (rows of L) of the primitive Jacobian of 1D ideal MHD
+ * for w = (rho, v_n, v_t1, v_t2, p, B_t1, B_t2) with normal field bn, in the
+ * normalisation of Roe & Balsara (1996): with a^2 = gamma p / rho, the fast
+ * and slow speeds c_f, c_s and the Alfven speed |bn|/sqrt(rho),
+ *   alpha_f^2 = (a^2 - c_s^2)/(c_f^2 - c_s^2), alpha_s^2 = (c_f^2 - a^2)/(c_f^2 - c_s^2)
+ *   (alpha_f = 1, alpha_s = 0 when c_f = c_s up to 1e-12),
+ *   beta = B_t/|B_t| ((1, 1)/sqrt 2 when |B_t| vanishes up to 1e-12),
+ *   sgn(bn) = 1 for bn >= 0.
+ * Waves in the order fast-, Alfven-, slow-, entropy, slow+, Alfven+, fast+. */
+void orc_char_eig(const double *w, double bn, double gamma, double *lam, double *R, double *L) {
+  double rho = w[0], u = w[1], p = w[4];
+  double a2 = gamma * p / rho, a = sqrt(a2), sr = sqrt(rho);
+  double bnr = bn / sr, b1 = w[5] / sr, b2 = w[6] / sr;
+  double bt2 = b1 * b1 + b2 * b2, bsq = bnr * bnr + bt2;
+  double disc = (a2 + bsq) * (a2 + bsq) - 4.0 * a2 * bnr * bnr;
+  if (disc < 0.0) disc = 0.0;
+  double cf2 = 0.5 * (a2 + bsq + sqrt(disc)), cs2 = 0.5 * (a2 + bsq - sqrt(disc));
+  if (cs2 < 0.0) cs2 = 0.0;
+  double cf = sqrt(cf2), cs = sqrt(cs2), ca = fabs(bnr);
+  double bt = sqrt(bt2), be1, be2;
+  if (bt > 1e-12 * sqrt(a2 + bsq)) {
+    be1 = b1 / bt;
+    be2 = b2 / bt;
+  } else {
+    be1 = be2 = 1.0 / sqrt(2.0);
+  }
+  double af, as, d = cf2 - cs2;
+  if (d > 1e-12 * cf2) {
+    af = sqrt((a2 - cs2 > 0.0 ? a2 - cs2 : 0.0) / d);
+    as = sqrt((cf2 - a2 > 0.0 ? cf2 - a2 : 0.0) / d);
+  } else {
+    af = 1.0;
+    as = 0.0;
+  }
+  double sg = bn >= 0.0 ? 1.0 : -1.0;
+  for (int k = 0; k < 49; ++k) R[k] = L[k] = 0.0;
+#define RR(i, k) R[(i) * 7 + (k)]
+#define LL(k, i) L[(k) * 7 + (i)]
+  for (int side = -1; side <= 1; side += 2) {
+    double e = (double)side;
+    int f = side < 0 ? 0 : 6, al = side < 0 ? 1 : 5, sl = side < 0 ? 2 : 4;
+    lam[f] = u + e * cf;
+    RR(0, f) = rho * af; RR(1, f) = e * af * cf; RR(2, f) = -e * as * cs * be1 * sg; RR(3, f) = -e * as * cs * be2 * sg;
+    RR(4, f) = rho * af * a2; RR(5, f) = as * a * sr * be1; RR(6, f) = as * a * sr * be2;
+    LL(f, 1) = e * af * cf / (2.0 * a2); LL(f, 2) = -e * as * cs * be1 * sg / (2.0 * a2);
+    LL(f, 3) = -e * as * cs * be2 * sg / (2.0 * a2); LL(f, 4) = af / (2.0 * rho * a2);
+    LL(f, 5) = as * be1 / (2.0 * sr * a); LL(f, 6) = as * be2 / (2.0 * sr * a);
+    lam[sl] = u + e * cs;
+    RR(0, sl) = rho * as; RR(1, sl) = e * as * cs; RR(2, sl) = e * af * cf * be1 * sg; RR(3, sl) = e * af * cf * be2 * sg;
+    RR(4, sl) = rho * as * a2; RR(5, sl) = -af * a * sr * be1; RR(6, sl) = -af * a * sr * be2;
+    LL(sl, 1) = e * as * cs / (2.0 * a2); LL(sl, 2) = e * af * cf * be1 * sg / (2.0 * a2);
+    LL(sl, 3) = e * af * cf * be2 * sg / (2.0 * a2); LL(sl, 4) = as / (2.0 * rho * a2);
+    LL(sl, 5) = -af * be1 / (2.0 * sr * a); LL(sl, 6) = -af * be2 / (2.0 * sr * a);
+    lam[al] = u + e * ca;
+    RR(2, al) = e * be2 * sg; RR(3, al) = -e * be1 * sg; RR(5, al) = -sr * be2; RR(6, al) = sr * be1;
+    LL(al, 2) = e * be2 * sg / 2.0; LL(al, 3) = -e * be1 * sg / 2.0;
+    LL(al, 5) = -be2 / (2.0 * sr); LL(al, 6) = be1 / (2.0 * sr);
+  }
+  lam[3] = u;
+  RR(0, 3) = 1.0;
+  LL(3, 0) = 1.0;
+  LL(3, 4) = -1.0 / a2;
+#undef RR
+#undef LL
+}
+
+/* MC limiter of a difference pair: sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2)
+ * when dm dp > 0, else 0 (orc_mc_slope on the differences). */
+static double mc_lim(double dm, double dp) {
+  if (dm * dp <= 0.0) return 0.0;
+  double a = 2.0 * fabs(dm), b = 2.0 * fabs(dp), c = 0.5 * fabs(dm + dp);
+  double m = a < b ? a : b;
+  m = m < c ? m : c;
+  return dp > 0.0 ? m : -m;
+}
+
+/* Characteristic MC slope of the middle cell of (wm, w0, wp), rotated
+ * primitives: the differences projected on the left eigenvectors of the
+ * middle cell, limited wave by wave, projected back with its right
+ * eigenvectors.  bn0: the middle cell's cell-centred normal field. */
+void orc_char_slope(const double *wm, const double *w0, const double *wp, double bn0, double gamma, double *slope) {
+  double lam[7], R[49], L[49], dm[7], dp[7], cm[7], cp[7], dc[7];
+  orc_char_eig(w0, bn0, gamma, lam, R, L);
+  for (int v = 0; v < 7; ++v) {
+    dm[v] = w0[v] - wm[v];
+    dp[v] = wp[v] - w0[v];
+  }
+  for (int k = 0; k < 7; ++k) {
+    cm[k] = cp[k] = 0.0;
+    for (int v = 0; v < 7; ++v) {
+      cm[k] += L[k * 7 + v] * dm[v];
+      cp[k] += L[k * 7 + v] * dp[v];
+    }
+    dc[k] = mc_lim(cm[k], cp[k]);
+  }
+  for (int v = 0; v < 7; ++v) {
+    slope[v] = 0.0;
+    for (int k = 0; k < 7; ++k) slope[v] += R[v * 7 + k] * dc[k];
+  }
+}
+
 typedef struct {
   const orc_cfg *c;
   int n[3];      /* interior cells */
@@ -487,9 +594,15 @@ static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7
         rotated(g, W, d, q0 + st, wp1);
         /* left cell (I-1): slopes from I-2, I-1, I;  right cell (I): I-1, I, I+1 */
         double sL[7], sR[7], wl[7], wr[7];
-        for (int v = 0; v < 7; ++v) {
-          sL[v] = orc_mc_slope(wm2[v], wm1[v], w0[v]);
-          sR[v] = orc_mc_slope(wm1[v], w0[v], wp1[v]);
+        if (c->recon == 1) {
+          /* characteristic slopes with each cell's own cell-centred normal field */
+          orc_char_slope(wm2, wm1, w0, W[5 + d][q0 - st], c->gamma, sL);
+          orc_char_slope(wm1, w0, wp1, W[5 + d][q0], c->gamma, sR);
+        } else {
+          for (int v = 0; v < 7; ++v) {
+            sL[v] = orc_mc_slope(wm2[v], wm1[v], w0[v]);
+            sR[v] = orc_mc_slope(wm1[v], w0[v], wp1[v]);
+          }
         }
         for (int v = 0; v < 7; ++v) {
           wl[v] = wm1[v] + 0.5 * sL[v];
