@@ -346,10 +346,14 @@ void orc_char_eig(const double *w, double bn, double gamma, double *lam, double 
   double a2 = gamma * p / rho, a = sqrt(a2), sr = sqrt(rho);
   double bnr = bn / sr, b1 = w[5] / sr, b2 = w[6] / sr;
   double bt2 = b1 * b1 + b2 * b2, bsq = bnr * bnr + bt2;
-  double disc = (a2 + bsq) * (a2 + bsq) - 4.0 * a2 * bnr * bnr;
-  if (disc < 0.0) disc = 0.0;
-  double cf2 = 0.5 * (a2 + bsq + sqrt(disc)), cs2 = 0.5 * (a2 + bsq - sqrt(disc));
-  if (cs2 < 0.0) cs2 = 0.0;
+  /* the same quantities in forms without cancellation: D = (a^2+b^2)^2 -
+   * 4 a^2 b_n^2 = (a^2-b^2)^2 + 4 a^2 b_t^2, c_f^2 - c_s^2 = sqrt D,
+   * c_f^2 - a^2 = (b^2 - a^2 + sqrt D)/2, a^2 - c_s^2 = (a^2 - b^2 + sqrt D)/2,
+   * c_s^2 = a^2 b_n^2 / c_f^2 (so that alpha_s is not the square root of a
+   * rounding residue when B_t vanishes) */
+  double sq = sqrt((a2 - bsq) * (a2 - bsq) + 4.0 * a2 * bt2);
+  double cf2 = 0.5 * (a2 + bsq + sq);
+  double cs2 = cf2 > 0.0 ? a2 * bnr * bnr / cf2 : 0.0;
   double cf = sqrt(cf2), cs = sqrt(cs2), ca = fabs(bnr);
   double bt = sqrt(bt2), be1, be2;
   if (bt > 1e-12 * sqrt(a2 + bsq)) {
@@ -358,10 +362,11 @@ void orc_char_eig(const double *w, double bn, double gamma, double *lam, double 
   } else {
     be1 = be2 = 1.0 / sqrt(2.0);
   }
-  double af, as, d = cf2 - cs2;
-  if (d > 1e-12 * cf2) {
-    af = sqrt((a2 - cs2 > 0.0 ? a2 - cs2 : 0.0) / d);
-    as = sqrt((cf2 - a2 > 0.0 ? cf2 - a2 : 0.0) / d);
+  double af, as;
+  if (sq > 1e-12 * cf2) {
+    double fa = 0.5 * (bsq - a2 + sq), as2 = 0.5 * (a2 - bsq + sq);   /* c_f^2 - a^2, a^2 - c_s^2 */
+    af = sqrt((as2 > 0.0 ? as2 : 0.0) / sq);
+    as = sqrt((fa > 0.0 ? fa : 0.0) / sq);
   } else {
     af = 1.0;
     as = 0.0;
