@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
+    p.add_argument("--recon", default="primitive", choices=["primitive", "characteristic"],
+                   help="reconstruction of single-box workloads")
     p.add_argument("--switch-faces", type=int, default=10_000_000, help="training faces of the learned switch")
     p.add_argument("--switch-steps", type=int, default=3000, help="Adam steps of the learned switch")
     return p.parse_args()
@@ -251,7 +253,10 @@ def workload_config(args):
         "blast_batch64": f"blast_batch_{args.n}: {args.n} outflow MHD blast boxes, 32-128 cells per axis "
                          f"log-uniform, one persistent launch per call, autotuned tile, per-box CFL 0.4",
     }[args.workload]
-    return {"workload": text, "precision": args.precision, "n": args.n}
+    out = {"workload": text, "precision": args.precision, "n": args.n}
+    if getattr(args, "recon", "primitive") != "primitive":
+        out["recon"] = args.recon
+    return out
 
 
 def run_reference(args):
@@ -309,7 +314,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     riemann = "learned" if learned else ("hll" if args.workload == "riemann2d3200_hll" else "hlld")
     solver = mhd.Solver(box, precision=args.precision, riemann=riemann, tile=tile,
-                        stream=stream.cuda_stream, integrator="rk3" if rk3 else "rk2")
+                        stream=stream.cuda_stream, integrator="rk3" if rk3 else "rk2", recon=args.recon)
     if learned:
         solver.set_switch(sw.block.data_ptr(), tau)
     solver.set_state(box.cell, box.face)
@@ -354,7 +359,8 @@ def run_ours(args):
     per_launch_ms = stage_ms[k] / max(launches[k], 1)
     alg_bytes = stage_bytes[k] * box.ncell
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    kname = "stage_kernel" + ("_learned" if learned else "") + ("_rk3" if rk3 else "")
+    kname = "stage_kernel" + ("_learned" if learned else "") + ("_rk3" if rk3 else "") + \
+        ("_char" if args.recon == "characteristic" else "")
     tag = f"{kname}<{args.precision},{k + 1}>@{box.name}"
     traffic, src = traffic_from_profiles(tag)
     elem = 4 if args.precision == "fp32" else 8
@@ -413,7 +419,7 @@ def run_ours(args):
         cmp = {}
         dt = solver.cfl_dt()
         ref = mhd.Solver(box, precision="fp64", riemann="hll" if riemann == "hll" else "hlld", stream=stream.cuda_stream,
-                         integrator="rk3" if rk3 else "rk2")
+                         integrator="rk3" if rk3 else "rk2", recon=args.recon)
         ref.set_state(box.cell, box.face)
         ref.step(dt, 1)
         ref.set_state(box.cell, box.face)

@@ -74,6 +74,11 @@ extern "C" {
 #define MHD_RK3 1 /* three-stage SSP Runge-Kutta of Shu & Osher (1988), the paper's default (Sec. 2.2);
                      16x8 tile, single boxes, HLLD or HLL */
 
+#define MHD_RECON_PRIMITIVE 0      /* MC-limited PLM of the primitives (default) */
+#define MHD_RECON_CHARACTERISTIC 1 /* MC-limited PLM of the characteristic variables (the paper's alternative,
+                                      Sec. 2.2; Roe-Balsara eigenvectors); 16x8 tile, RK2, HLLD or HLL,
+                                      single boxes */
+
 #define MHD_EMF_UPWIND 0 /* Gardiner & Stone (2005) upwind contact average */
 #define MHD_EMF_MEAN 1   /* arithmetic mean of the four face EMFs (debug) */
 
@@ -90,6 +95,7 @@ typedef struct {
   double p_floor;          /* pressure floor (1e-10) */
   int tile_x, tile_y, tile_z; /* tile of the fused stage kernel; 0 = default */
   int integrator;          /* MHD_RK2 | MHD_RK3 */
+  int recon;               /* MHD_RECON_PRIMITIVE | MHD_RECON_CHARACTERISTIC */
 } mhd_config;
 
 typedef struct {

@@ -32,6 +32,12 @@ cudaError_t launch_stage_rk3_fp32(int, unsigned, size_t, cudaStream_t, const Geo
 cudaError_t set_smem_rk3_fp64(size_t);
 cudaError_t set_smem_rk3_mixed(size_t);
 cudaError_t set_smem_rk3_fp32(size_t);
+cudaError_t launch_stage_char_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_char_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_char_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t set_smem_char_fp64(size_t);
+cudaError_t set_smem_char_mixed(size_t);
+cudaError_t set_smem_char_fp32(size_t);
 cudaError_t set_smem_learned_fp64(size_t);
 cudaError_t set_smem_learned_mixed(size_t);
 cudaError_t set_smem_learned_fp32(size_t);
@@ -46,6 +52,13 @@ cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nb, size_
       case P_FP64: return launch_stage_rk3_fp64(stage, nb, smem, st, g, a);
       case P_MIXED: return launch_stage_rk3_mixed(stage, nb, smem, st, g, a);
       default: return launch_stage_rk3_fp32(stage, nb, smem, st, g, a);
+    }
+  }
+  if (g.recon == 1) {
+    switch (prec) {
+      case P_FP64: return launch_stage_char_fp64(stage, nb, smem, st, g, a);
+      case P_MIXED: return launch_stage_char_mixed(stage, nb, smem, st, g, a);
+      default: return launch_stage_char_fp32(stage, nb, smem, st, g, a);
     }
   }
   if (g.riemann == 2) {
@@ -68,6 +81,13 @@ cudaError_t launch_prims(int prec, unsigned nb, cudaStream_t st, const Geo& g, c
     case P_FP64: return launch_prims_fp64(nb, st, g, a);
     case P_MIXED: return launch_prims_mixed(nb, st, g, a);
     default: return launch_prims_fp32(nb, st, g, a);
+  }
+}
+cudaError_t stage_set_smem_char(int prec, size_t bytes) {
+  switch (prec) {
+    case P_FP64: return set_smem_char_fp64(bytes);
+    case P_MIXED: return set_smem_char_mixed(bytes);
+    default: return set_smem_char_fp32(bytes);
   }
 }
 cudaError_t stage_set_smem_rk3(int prec, size_t bytes) {
@@ -212,6 +232,11 @@ static int validate(const mhd_config* c, mhd_handle* h) {
     return fail(h, MHD_ERR_INVALID, "SSP-RK3 is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
   if (c->integrator == MHD_RK3 && c->riemann == MHD_LEARNED)
     return fail(h, MHD_ERR_INVALID, "the learned switch runs with the RK2 integrator");
+  if (c->recon != MHD_RECON_PRIMITIVE && c->recon != MHD_RECON_CHARACTERISTIC)
+    return fail(h, MHD_ERR_INVALID, "unknown reconstruction");
+  if (c->recon == MHD_RECON_CHARACTERISTIC &&
+      (tx != 16 || ty != 8 || c->integrator != MHD_RK2 || c->riemann == MHD_LEARNED))
+    return fail(h, MHD_ERR_INVALID, "characteristic reconstruction runs on the 16x8 tile with RK2 and HLLD or HLL");
   if (stage_smem_bytes(c->precision, tx, ty) > 227 * 1024)
     return fail(h, MHD_ERR_INVALID, "tile %dx%d needs %zu B of shared memory (> 227 KB)", tx, ty,
                 stage_smem_bytes(c->precision, tx, ty));
@@ -229,6 +254,7 @@ static void fill_geo(const mhd_config* c, Geo* g) {
   g->gamma = c->gamma; g->rho_floor = c->rho_floor; g->p_floor = c->p_floor; g->cfl = c->cfl;
   g->emf_mean = c->emf == MHD_EMF_MEAN;
   g->riemann = c->riemann == MHD_HLL ? 1 : (c->riemann == MHD_LEARNED ? 2 : 0);
+  g->recon = c->recon == MHD_RECON_CHARACTERISTIC ? 1 : 0;
   g->deadband = c->precision == MHD_FP64 ? 1e-10 : 1e-6;
   if (getenv("MHD_DEADBAND")) g->deadband = atof(getenv("MHD_DEADBAND"));
   resolve_tile(c, &g->TX, &g->TY, &g->TZ);
@@ -294,6 +320,8 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   if (e == cudaSuccess) e = stage_set_smem(cfg->precision, h->geo.TX, h->geo.TY, h->smem_bytes);
   if (e == cudaSuccess && cfg->riemann == MHD_LEARNED) e = stage_set_smem_learned(cfg->precision, h->smem_bytes);
   if (e == cudaSuccess && cfg->integrator == MHD_RK3) e = stage_set_smem_rk3(cfg->precision, h->smem_bytes);
+  if (e == cudaSuccess && cfg->recon == MHD_RECON_CHARACTERISTIC)
+    e = stage_set_smem_char(cfg->precision, h->smem_bytes);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     fail(nullptr, MHD_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
@@ -845,6 +873,8 @@ extern "C" int mhd_batch_create(int nbox, const mhd_config* cfgs, void* cuda_str
       return bfail(nullptr, MHD_ERR_INVALID, "batches solve with HLLD or HLL; the learned switch is single-box only");
     if (cfgs[i].integrator != MHD_RK2)
       return bfail(nullptr, MHD_ERR_INVALID, "batches step with the RK2 integrator; SSP-RK3 is single-box only");
+    if (cfgs[i].recon != MHD_RECON_PRIMITIVE)
+      return bfail(nullptr, MHD_ERR_INVALID, "batches reconstruct the primitives; characteristic PLM is single-box only");
   }
   mhd_batch* b = new (std::nothrow) mhd_batch();
   if (!b) return bfail(nullptr, MHD_ERR_NOMEM, "host allocation failed");

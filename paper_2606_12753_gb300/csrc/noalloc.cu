@@ -62,8 +62,8 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, void* cuda_stream, const 
   for (int d = 0; d < 3; ++d)
     if (!face_in[d] || !face_out[d]) return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s", "null face array");
   if (dt != dt) return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s", "dt is NaN");
-  if (cfg->integrator != MHD_RK2)
-    return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s", "runs the RK2 integrator only");
+  if (cfg->integrator != MHD_RK2 || cfg->recon != MHD_RECON_PRIMITIVE)
+    return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s", "runs RK2 with primitive reconstruction only");
   int rc = internal_validate(cfg);
   if (rc) return rc;   // message already set
   Geo g;

@@ -285,6 +285,119 @@ __host__ __device__ __forceinline__ R edge_emf(R fa_m, R fa_p, R ma_m, R ma_p, R
   return avg + R(0.25) * (db_minus - db_plus) + R(0.25) * (da_minus - da_plus);
 }
 
+// MC limiter of a difference pair: sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2)
+// when dm and dp have the same sign, else 0.
+template <typename R>
+__host__ __device__ __forceinline__ R mc_lim(R dm, R dp) {
+  R m = fmin_(R(2) * fmin_(rabs(dm), rabs(dp)), R(0.5) * rabs(dm + dp));
+  m = opposite_signs(dm, dp) ? R(0) : m;
+  return copysign_(m, dp);
+}
+
+// Characteristic MC slope of the middle cell w0 of (wm, w0, wp), rotated
+// primitives (rho, v_n, v_t1, v_t2, p, B_t1, B_t2), bn0 the middle cell's
+// cell-centred normal field.  The one-sided differences are projected on the
+// left eigenvectors of the primitive Jacobian at w0, limited wave by wave and
+// projected back with the right eigenvectors (Roe & Balsara 1996
+// normalisation: alpha_f, alpha_s, beta = B_t/|B_t|, sgn(bn) = 1 for bn >= 0;
+// alpha_f = 1 when c_f = c_s and beta = (1, 1)/sqrt 2 when |B_t| vanishes,
+// both to the precision's degeneracy tolerance).  Each +/- wave pair shares
+// an even and an odd part of its projection, which the code forms once.
+template <typename R>
+__host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, const R* wp, R bn0, R gamma,
+                                                    R* slope) {
+  const R rho = w0[0];
+  const R ir = R(1) / rho;
+  const R a2 = gamma * w0[4] * ir, a = rsqrt_(a2), sr = rsqrt_(rho), isr = R(1) / sr;
+  const R bnr = bn0 * isr, b1 = w0[5] * isr, b2 = w0[6] * isr;
+  const R bt2 = b1 * b1 + b2 * b2, bsq = bnr * bnr + bt2;
+  // forms without cancellation: c_f^2 - c_s^2 = sqrt((a^2-b^2)^2 + 4 a^2 b_t^2),
+  // c_s^2 = a^2 b_n^2 / c_f^2, and below c_f^2 - a^2, a^2 - c_s^2 as half-sums
+  // with that root (alpha_s is otherwise the root of a rounding residue when
+  // B_t vanishes)
+  const R sq = rsqrt_((a2 - bsq) * (a2 - bsq) + R(4) * a2 * bt2);
+  const R cf2 = R(0.5) * (a2 + bsq + sq);
+  const R cs2 = cf2 > R(0) ? a2 * bnr * bnr / cf2 : R(0);
+  const R cf = rsqrt_(cf2), cs = rsqrt_(cs2), bt = rsqrt_(bt2);
+  R be1, be2;
+  if (bt > Eps<R>::degen * rsqrt_(a2 + bsq)) {
+    const R ib = R(1) / bt;
+    be1 = b1 * ib;
+    be2 = b2 * ib;
+  } else {
+    be1 = be2 = R(0.70710678118654752440);
+  }
+  R af, as;
+  if (sq > Eps<R>::degen * cf2) {
+    const R id = R(1) / sq;
+    const R fa = R(0.5) * (bsq - a2 + sq), as2 = R(0.5) * (a2 - bsq + sq);   // c_f^2 - a^2, a^2 - c_s^2
+    af = rsqrt_((as2 > R(0) ? as2 : R(0)) * id);
+    as = rsqrt_((fa > R(0) ? fa : R(0)) * id);
+  } else {
+    af = R(1);
+    as = R(0);
+  }
+  const R sg = bn0 >= R(0) ? R(1) : R(-1);
+  const R i2a2 = R(0.5) / a2, i2r = i2a2 * ir, i2sa = R(0.5) * isr / a, i2s = R(0.5) * isr;
+  R dc[7];   // limited wave amplitudes: f-, a-, s-, e, s+, a+, f+
+  {
+    R m[7], q[7];
+    const R* pairs[2][2] = {{wm, w0}, {w0, wp}};
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      R d[7];
+#pragma unroll
+      for (int v = 0; v < 7; ++v) d[v] = pairs[side][1][v] - pairs[side][0][v];
+      const R t = be1 * d[2] + be2 * d[3], bb = be1 * d[5] + be2 * d[6];
+      const R xf = (af * cf * d[1] - as * cs * sg * t) * i2a2, yf = af * d[4] * i2r + as * bb * i2sa;
+      const R xs = (as * cs * d[1] + af * cf * sg * t) * i2a2, ys = as * d[4] * i2r - af * bb * i2sa;
+      const R xa = R(0.5) * sg * (be2 * d[2] - be1 * d[3]), ya = (be1 * d[6] - be2 * d[5]) * i2s;
+      R* c = side == 0 ? m : q;
+      c[0] = yf - xf;
+      c[1] = ya - xa;
+      c[2] = ys - xs;
+      c[3] = d[0] - d[4] / a2;
+      c[4] = ys + xs;
+      c[5] = ya + xa;
+      c[6] = yf + xf;
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) dc[k] = mc_lim(m[k], q[k]);
+  }
+  const R Fp = dc[6] + dc[0], Fm = dc[6] - dc[0];
+  const R Sp = dc[4] + dc[2], Sm = dc[4] - dc[2];
+  const R Ap = dc[5] + dc[1], Am = dc[5] - dc[1];
+  slope[0] = rho * (af * Fp + as * Sp) + dc[3];
+  slope[1] = af * cf * Fm + as * cs * Sm;
+  const R tv = af * cf * Sm - as * cs * Fm;
+  slope[2] = sg * (be1 * tv + be2 * Am);
+  slope[3] = sg * (be2 * tv - be1 * Am);
+  slope[4] = rho * a2 * (af * Fp + as * Sp);
+  const R tb = a * sr * (as * Fp - af * Sp);
+  slope[5] = be1 * tb - sr * be2 * Ap;
+  slope[6] = be2 * tb + sr * be1 * Ap;
+}
+
+// Characteristic PLM of a face: as plm_face, with the slopes of c1 and c2
+// taken in characteristic variables (bn1, bn2: their cell-centred normal
+// fields).
+template <typename R>
+__host__ __device__ __forceinline__ void plm_face_char(const R* c0, const R* c1, const R* c2, const R* c3, R bn1,
+                                                       R bn2, R gamma, R* wl, R* wr, R rho_floor, R p_floor) {
+  R sl[7], sr_[7];
+  char_slope(c0, c1, c2, bn1, gamma, sl);
+  char_slope(c1, c2, c3, bn2, gamma, sr_);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    wl[q] = c1[q] + R(0.5) * sl[q];
+    wr[q] = c2[q] - R(0.5) * sr_[q];
+  }
+  wl[0] = rmax(wl[0], rho_floor);
+  wr[0] = rmax(wr[0], rho_floor);
+  wl[4] = rmax(wl[4], p_floor);
+  wr[4] = rmax(wr[4], p_floor);
+}
+
 // Reconstruct the two states of a face from four cells along the normal
 // (c0, c1 | c2, c3), 7 rotated primitives each; face values of rho and p are
 // floored (MC keeps them between the neighbouring cell values, so the floor

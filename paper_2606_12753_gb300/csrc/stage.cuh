@@ -45,6 +45,7 @@ struct Geo {
   double gamma, rho_floor, p_floor, cfl;
   int emf_mean;
   int riemann;     // 0 HLLD, 1 HLL, 2 learned
+  int recon;       // 0 MC on the primitives, 1 MC on the characteristic variables
   double deadband; // relative deadband on the mass flux orienting the upwind EMF
   int TX, TY, TZ;
   int ntx, nty, nchunk;

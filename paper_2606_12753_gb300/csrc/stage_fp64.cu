@@ -89,4 +89,23 @@ cudaError_t set_smem_rk3_fp64(size_t bytes) {
   return e;
 }
 
+// Characteristic reconstruction (RK2 stages, 16 x 8 tile).
+cudaError_t launch_stage_char_fp64(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
+                                 const StageArgs& args) {
+  if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
+  if (stage == 1) stage_kernel_char<P_FP64, 1, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  else if (stage == 2) stage_kernel_char<P_FP64, 2, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t set_smem_char_fp64(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel_char<P_FP64, 1, 16, 8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage_kernel_char<P_FP64, 2, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  return e;
+}
+
 }  // namespace mhd

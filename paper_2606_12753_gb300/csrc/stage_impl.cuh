@@ -130,8 +130,14 @@ __device__ void cell_prims(const Geo& g, const StageArgs& a, double dt, int i, i
   recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], bxl, bxh, byl, byh, bzl, bzh, w, rho_hit, p_hit);
 }
 
-template <int PREC, int STAGE, int TX, int TY, bool LEARN = false>
+// Flux modes of the stage kernel: plain (HLLD or HLL by Geo::riemann), the
+// learned HLL/HLLD switch, characteristic reconstruction.
+enum { FM_PLAIN = 0, FM_LEARNED = 1, FM_CHAR = 2 };
+
+template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN>
 struct StageKernel {
+  static constexpr bool LEARN = MODE == FM_LEARNED;
+  static constexpr bool CHAR = MODE == FM_CHAR;
   using R = typename Prec<PREC>::R;
   using S = typename Prec<PREC>::S;
   using K = typename Prec<PREC>::K;
@@ -194,6 +200,15 @@ struct StageKernel {
     for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
       R c[4][7], wl[7], wr[7], f[7], bn, cm;
       int o;
+      if (CHAR) {
+        R bnc[2];
+        const int D = item_stencil(sm, k, q, nZ, w, c, bn, o, bnc);
+        plm_face_char(c[0], c[1], c[2], c[3], bnc[0], bnc[1], gam, wl, wr, (R)g.rho_floor, (R)g.p_floor);
+        if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
+        else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
+        store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
+        continue;
+      }
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
       plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
       if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
@@ -223,8 +238,10 @@ struct StageKernel {
   // then the x- and y-faces of plane q): the four cells across the face in
   // its rotated order and the normal field.  Returns the face's axis and its
   // slot o in that axis' flux arrays.
+  // With bnc (characteristic reconstruction) also the cell-centred normal
+  // field of the face's two cells.
   static __device__ __forceinline__ int item_stencil(const R* sm, int k, int q, int nZ, int w, R (&c)[4][7], R& bn,
-                                                     int& o) {
+                                                     int& o, R* bnc = nullptr) {
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
     const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
     if (w < nZ) {
@@ -233,6 +250,10 @@ struct StageKernel {
 #pragma unroll
       for (int s = 0; s < 4; ++s) gather<2>(sm + T::oP + ((k - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
       bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
+      if (bnc) {
+        bnc[0] = sm[T::oP + (k & 3) * 8 * T::nR + 7 * T::nR + r];
+        bnc[1] = sm[T::oP + ((k + 1) & 3) * 8 * T::nR + 7 * T::nR + r];
+      }
       o = w;
       return 2;
     }
@@ -243,6 +264,10 @@ struct StageKernel {
 #pragma unroll
       for (int s = 0; s < 4; ++s) gather<0>(Pq, T::nR, r - 2 + s, c[s]);
       bn = BNq[r];
+      if (bnc) {
+        bnc[0] = Pq[5 * T::nR + r - 1];
+        bnc[1] = Pq[5 * T::nR + r];
+      }
       return 0;
     }
     o = w - nZ - T::nX;
@@ -251,6 +276,10 @@ struct StageKernel {
 #pragma unroll
     for (int s = 0; s < 4; ++s) gather<1>(Pq, T::nR, r + (s - 2) * W, c[s]);
     bn = BNq[T::nR + r];
+    if (bnc) {
+      bnc[0] = Pq[6 * T::nR + r - W];
+      bnc[1] = Pq[6 * T::nR + r];
+    }
     return 1;
   }
 
@@ -678,7 +707,14 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? (TX * TY <= 64 ? 2 : 1) 
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_learned(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, true>::run_item(g, a, blockIdx.x, smem_raw);
+  StageKernel<PREC, STAGE, TX, TY, FM_LEARNED>::run_item(g, a, blockIdx.x, smem_raw);
+}
+
+// The same stage with characteristic reconstruction.
+template <int PREC, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char(Geo g, StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageKernel<PREC, STAGE, TX, TY, FM_CHAR>::run_item(g, a, blockIdx.x, smem_raw);
 }
 
 // Primitives (and the CFL max) of a state set from outside: one thread per cell.

@@ -23,6 +23,8 @@ MHD_FP64, MHD_MIXED, MHD_FP32 = 0, 1, 2
 MHD_HLLD, MHD_HLL, MHD_LEARNED = 0, 1, 2
 MHD_EMF_UPWIND, MHD_EMF_MEAN = 0, 1
 MHD_RK2, MHD_RK3 = 0, 1
+MHD_RECON_PRIMITIVE, MHD_RECON_CHARACTERISTIC = 0, 1
+RECONS = {"primitive": MHD_RECON_PRIMITIVE, "characteristic": MHD_RECON_CHARACTERISTIC}
 INTEGRATORS = {"rk2": MHD_RK2, "rk3": MHD_RK3}
 
 PRECISIONS = {"fp64": MHD_FP64, "mixed": MHD_MIXED, "fp32": MHD_FP32}
@@ -37,7 +39,7 @@ class mhd_config(C.Structure):
                 ("precision", C.c_int), ("riemann", C.c_int), ("emf", C.c_int),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
-                ("integrator", C.c_int)]
+                ("integrator", C.c_int), ("recon", C.c_int)]
 
 
 class mhd_stats(C.Structure):
@@ -257,7 +259,7 @@ class Solver:
     bc, gamma (and optionally cfl) -- e.g. ``inputs.Box``."""
 
     def __init__(self, box, precision="fp64", riemann="hlld", emf="upwind", tile=(0, 0, 0),
-                 stream=None, cfl=None, rho_floor=1e-10, p_floor=1e-10, integrator="rk2"):
+                 stream=None, cfl=None, rho_floor=1e-10, p_floor=1e-10, integrator="rk2", recon="primitive"):
         c = mhd_default_config(box.nx, box.ny, box.nz)
         c.dx, c.dy, c.dz = box.dx, box.dy, box.dz
         c.gamma = box.gamma
@@ -269,6 +271,7 @@ class Solver:
         c.rho_floor, c.p_floor = rho_floor, p_floor
         c.tile_x, c.tile_y, c.tile_z = tile
         c.integrator = INTEGRATORS[integrator] if isinstance(integrator, str) else integrator
+        c.recon = RECONS[recon] if isinstance(recon, str) else recon
         self.cfg = c
         self.dims = (box.nx, box.ny, box.nz)
         self.bc = tuple(box.bc)

@@ -112,3 +112,27 @@ def test_rk3_validation():
     h = mhd.C.c_void_p()
     rc = mhd.load().mhd_batch_create(2, cfgs, None, mhd.C.byref(h))
     assert rc == mhd.MHD_ERR_INVALID
+
+
+def test_char_recon_validation():
+    from paper_2606_12753_gb300 import inputs as I
+    c = mhd.mhd_default_config(32, 32, 32)
+    assert c.recon == mhd.MHD_RECON_PRIMITIVE
+    c.recon = mhd.MHD_RECON_CHARACTERISTIC
+    for field, value in (("tile_x", 8), ("integrator", mhd.MHD_RK3), ("riemann", mhd.MHD_LEARNED)):
+        d = mhd.mhd_config.from_buffer_copy(c)
+        setattr(d, field, value)
+        if field == "tile_x":
+            d.tile_y = 8
+        with pytest.raises(mhd.MHDError) as ei:
+            mhd.mhd_create(d)
+        assert "characteristic" in str(ei.value) or "16x8" in str(ei.value) or "RK2" in str(ei.value)
+    c.recon = 5
+    with pytest.raises(mhd.MHDError):
+        mhd.mhd_create(c)
+    boxes = [I.uniform_state((16, 16, 16)), I.uniform_state((8, 16, 16))]
+    cfgs = (mhd.mhd_config * 2)(*[mhd.box_config(b, "fp32") for b in boxes])
+    for k in range(2):
+        cfgs[k].recon = mhd.MHD_RECON_CHARACTERISTIC
+    h = mhd.C.c_void_p()
+    assert mhd.load().mhd_batch_create(2, cfgs, None, mhd.C.byref(h)) == mhd.MHD_ERR_INVALID
