@@ -69,6 +69,24 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(value: float, world: int, device="cuda") -> float:
+    """MAX of a per-rank float over all ranks of the process group (one
+    collective; the timing rule takes the slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job Mcell-updates/s: every rank advances its own replica of the
+    workload (replicas only: the single-box path does not shard), timed by
+    the slowest rank."""
+    return world * cells_per_rank * steps / (ms_max / 1e3) / 1e6
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -347,11 +365,8 @@ def run_ours(args):
     st = solver.stats()
     if st["status"] != 0:
         raise RuntimeError(f"device status {st['status']} after the timed steps")
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * box.ncell * args.steps / (ms_total / 1e3) / 1e6
+    ms_total = max_over_ranks(ms_total, world)
+    value = job_rate(box.ncell, args.steps, ms_total, world)
 
     peak, peak_kind = peaks()
     nst = len(stage_bytes)
@@ -498,6 +513,15 @@ def run_batch(args):
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
     from paper_2606_12753_gb300 import inputs as I
     from paper_2606_12753_gb300 import mhd
     boxes = I.blast_batch(args.n, seed=64)
@@ -510,7 +534,7 @@ def run_batch(args):
     tile, tune_ms = batch.autotune(trial_steps=3, cache_path=cache)
     clk = ClockSampler(local).start()
     batch.step(-1.0, args.warmup)
-    torch.cuda.synchronize()
+    barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     clk.mark_start()
@@ -520,11 +544,12 @@ def run_batch(args):
     stream.synchronize()
     clk.mark_end()
     clk.stop()
-    ms_total = e0.elapsed_time(e1)
+    barrier()
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world)
     st = batch.stats()
     if st["status"] != 0:
         raise RuntimeError(f"device status {st['status']} after the timed steps")
-    value = world * ncell * args.steps / (ms_total / 1e3) / 1e6
+    value = job_rate(ncell, args.steps, ms_total, world)
     peak, peak_kind = peaks()
     step_bytes = sum(STAGE_BYTES[args.precision]) * ncell
     achieved = step_bytes * args.steps / (ms_total / 1e3) / 1e9
@@ -536,7 +561,8 @@ def run_batch(args):
         "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision], "data": "synthetic",
         "config": {**workload_config(args), "cells": ncell, "tile": [tx, ty, tz], "work_items": items,
                    "persistent_grid": grid, "autotune_ms_per_step": tune_ms,
-                   "l2": "inputs larger than L2", "parallelism": "single GPU, all boxes in one launch"},
+                   "l2": "inputs larger than L2",
+                   "parallelism": (f"replicas x{world}, " if world > 1 else "") + "all boxes of a GPU in one launch"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": f"batch_kernel<{args.precision},{tx}x{ty}>@blast_batch_{args.n}",
                      "peak_kind": peak_kind},
@@ -547,6 +573,8 @@ def run_batch(args):
     batch.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def main():
