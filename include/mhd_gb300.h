@@ -9,13 +9,16 @@
  * no formulas; the arithmetic follows the methods it names:
  *   - primitive recovery p = (gamma-1)(E - |m|^2/(2 rho) - |B_c|^2/2), with the
  *     cell field B_c the mean of the cell's two staggered faces;
- *   - piecewise-linear reconstruction of (rho, v, p, B_t) with the MC limiter;
+ *   - piecewise-linear reconstruction of (rho, v, p, B_t) with the MC limiter,
+ *     on the primitives or (MHD_RECON_CHARACTERISTIC) on the characteristic
+ *     variables (the paper's "primitive (or characteristic) variables");
  *   - the HLLD Riemann flux (Miyoshi & Kusano 2005) on every x, y and z face,
  *     or HLL, or a learned per-face choice between the two;
  *   - the flux divergence of (rho, m, E);
  *   - edge EMFs by the upwind average of Gardiner & Stone (2005) and the
  *     staggered update dB/dt = -curl E (div B stays at rounding);
- *   - two-stage RK2 (Heun) with one dt per step;
+ *   - two-stage RK2 (Heun), or the paper's default three-stage SSP-RK3
+ *     (MHD_RK3), with one dt per step;
  *   - the CFL time step dt = cfl / max_cells sum_d (|v_d| + c_f,d)/Delta_d.
  *
  * Conventions
@@ -128,10 +131,11 @@ int mhd_set_state(mhd_handle* h, const void* const cell[5], const void* const fa
 /* Copy the current state out (same layout and pointer kinds); synchronises. */
 int mhd_get_state(mhd_handle* h, void* cell[5], void* face[3], int on_device);
 
-/* Advance nsteps RK2 steps.  dt > 0: that dt for every step.  dt <= 0: each
- * step takes the CFL dt of its own starting state, reduced on the device
- * (no host round trip).  Enqueues 2 kernels per step; synchronises once at
- * the end to read the status word. */
+/* Advance nsteps steps of the configured integrator (RK2 or SSP-RK3).
+ * dt > 0: that dt for every step.  dt <= 0: each step takes the CFL dt of its
+ * own starting state, reduced on the device (no host round trip).  Enqueues 2
+ * (RK2) or 3 (RK3) kernels per step; synchronises once at the end to read
+ * the status word. */
 int mhd_step(mhd_handle* h, double dt, int nsteps);
 
 /* Enqueue nsteps steps like mhd_step (dt <= 0: device-side CFL dt) without

@@ -1,4 +1,5 @@
-// Shared definitions of the fused RK2 stage kernels (ideal MHD, GB300 sm_103a).
+// Shared definitions of the fused Runge-Kutta stage kernels (ideal MHD, GB300
+// sm_103a).
 //
 // Data kept in HBM per box (SoA, x fastest, one packed allocation each):
 //   U[2]  conserved state, ping-pong (rho, mx, my, mz, E | Bx, By, Bz faces),
@@ -14,7 +15,8 @@
 // One RK2 (Heun) step = stage 1 (W(U^n) -> K1 = L(U^n), W(U*)) and stage 2
 // (W(U*) -> U^{n+1} = U^n + dt/2 (K1 + L(U*)), W(U^{n+1}), CFL max of
 // U^{n+1} for the next step).  U* = U^n + dt K1 is never stored: the ghost
-// faces of outflow boundaries rebuild it from U^n and K1.
+// faces of outflow boundaries rebuild it from U^n and K1.  An SSP-RK3 step
+// stores its two intermediate states (type S) and runs three stages.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

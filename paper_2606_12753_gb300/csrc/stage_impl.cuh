@@ -1,4 +1,6 @@
-// Fused z-marching RK2 stage kernel, templated on precision, stage and tile.
+// Fused z-marching Runge-Kutta stage kernel, templated on precision, stage
+// (RK2 stages 1-2, SSP-RK3 stages 3-5), tile and flux mode (plain, learned
+// HLL/HLLD switch, characteristic reconstruction).
 //
 // One CTA owns a TX x TY column of cells and marches along z through a chunk
 // of TZ planes.  Per output plane k:
@@ -6,13 +8,14 @@
 //      into a 4-plane shared-memory ring; periodic axes wrap by index, outflow
 //      ghost cells copy the nearest interior cell's primitives with the
 //      normal field on their faces extrapolated linearly (div B = 0);
-//   B  PLM-MC reconstruction + Riemann solve (HLLD / HLL) on the z-faces k+1/2
+//   B  PLM-MC reconstruction (primitive or characteristic) + Riemann solve
+//      (HLLD / HLL, or the learned choice between them) on the z-faces k+1/2
 //      and on the x- and y-faces of plane k+1 (one halo row across, for the
 //      edge EMFs), and the cell-centred EMF -v x B of plane k+1;
 //   C  flux divergence and the Gardiner-Stone edge EMFs E_z(k), E_x, E_y(k+1/2);
 //   D  new face values (-curl E), then per owned cell the new conserved state,
 //      its primitives (FP64 pressure recovery in the FP64/mixed forms) and,
-//      in stage 2, the CFL speed of U^{n+1}.
+//      in the last stage of a step, the CFL speed of U^{n+1}.
 // This is the chain Reconstruct -> HLLD_Solver -> RightHandSide -> CT_EMF ->
 // US of the paper's MHD step (Sec. 2.2, Table 2) fused into one pass per
 // RK stage.
