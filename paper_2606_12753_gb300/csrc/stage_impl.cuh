@@ -462,6 +462,66 @@ struct StageKernel {
     }
   }
 
+  // Phase C of a two-dimensional box (one periodic z cell).  The flux pass
+  // computed the x/y data of plane 1, which is plane 0 itself, into slot 1;
+  // the z-faces below and above a cell are one face, so the divergence drops
+  // their difference (exactly zero), and the edges E_x, E_y at k-1/2 and
+  // k+1/2 are one set, written to both slots.
+  static __device__ __forceinline__ void edges_2d(const Geo& g, R* sm) {
+    const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1];
+    R* DU0 = sm + T::oDU;
+    const R* HX = sm + T::oHX;
+    const R* HY = sm + T::oHY;
+    for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
+      const int i = c % TX, j = c / TX;
+      const int ixm = i + (TX + 1) * (j + 1), ixp = ixm + 1;
+      const int iym = (i + 1) + (TX + 2) * j, iyp = iym + (TX + 2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        DU0[v * T::nC + c] = -(HX[v * T::nX + ixp] - HX[v * T::nX + ixm]) * idx -
+                             (HY[v * T::nY + iyp] - HY[v * T::nY + iym]) * idy;
+    }
+    const bool mean = g.emf_mean != 0;
+    const R* XC = sm + T::oXC + 3 * T::nX;
+    const R* YC = sm + T::oYC + 3 * T::nY;
+    const R* ZC = sm + T::oZC;
+    const R* EC = sm + T::oEC + 3 * T::nZ;
+    R* EZ = sm + T::oEZ;
+    R* EX0 = sm + T::oEXY;
+    R* EY0 = EX0 + T::nE;
+    R* EX1 = sm + T::oEXY + 2 * T::nE;
+    R* EY1 = EX1 + T::nE;
+    constexpr int nX = T::nX, nY = T::nY, nZ = T::nZ;
+    for (int e = threadIdx.x; e < T::nE; e += blockDim.x) {
+      const int i = e % (TX + 1), j = e / (TX + 1);
+      {
+        const int xa = i + (TX + 1) * j, xb = xa + (TX + 1);
+        const int ya = i + (TX + 2) * j, yb = ya + 1;
+        const int c_mm = i + (TX + 2) * j, c_pm = c_mm + 1, c_mp = c_mm + (TX + 2), c_pp = c_mp + 1;
+        EZ[e] = edge_emf<R>(XC[xa], XC[xb], XC[2 * nX + xa], XC[2 * nX + xb], YC[nY + ya], YC[nY + yb],
+                            YC[2 * nY + ya], YC[2 * nY + yb], EC[2 * nZ + c_mm], EC[2 * nZ + c_pm],
+                            EC[2 * nZ + c_mp], EC[2 * nZ + c_pp], mean);
+      }
+      if (i < TX) {
+        const int ya = (i + 1) + (TX + 2) * j;
+        const int za = (i + 1) + (TX + 2) * j, zb = za + (TX + 2);
+        const R ex = edge_emf<R>(YC[ya], YC[ya], YC[2 * nY + ya], YC[2 * nY + ya], ZC[nZ + za], ZC[nZ + zb],
+                                 ZC[2 * nZ + za], ZC[2 * nZ + zb], EC[za], EC[zb], EC[za], EC[zb], mean);
+        EX0[e] = ex;
+        EX1[e] = ex;
+      }
+      if (j < TY) {
+        const int za = i + (TX + 2) * (j + 1), zb = za + 1;
+        const int xa = i + (TX + 1) * (j + 1);
+        const R ey = edge_emf<R>(ZC[za], ZC[zb], ZC[2 * nZ + za], ZC[2 * nZ + zb], XC[nX + xa], XC[nX + xa],
+                                 XC[2 * nX + xa], XC[2 * nX + xa], EC[nZ + za], EC[nZ + za], EC[nZ + zb],
+                                 EC[nZ + zb], mean);
+        EY0[e] = ey;
+        EY1[e] = ey;
+      }
+    }
+  }
+
   // new value of one conserved quantity from its increment l:
   // RK2 stage 1 U* = U^n + dt K1 (K1 = l rounded to K), stage 2 U^n + dt/2 (K1 + l);
   // RK3 (input state U_in): U1 = U_in + dt l, U2 = 3/4 U^n + 1/4 (U_in + dt l),
@@ -610,6 +670,32 @@ struct StageKernel {
     }
   }
 
+  // Counters, status and the CFL max of the item, one atomic per warp.
+  static __device__ __forceinline__ void finish(const StageArgs& a, unsigned nrho, unsigned np, unsigned nh,
+                                                unsigned nd, bool bad, R smax) {
+    const unsigned mask = 0xffffffffu;
+    nrho = __reduce_add_sync(mask, nrho);
+    np = __reduce_add_sync(mask, np);
+    const unsigned anybad = __any_sync(mask, bad);
+    double sm64 = (double)smax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sm64 = fmax(sm64, __shfl_xor_sync(mask, sm64, o));
+    if (LEARN) {
+      nh = __reduce_add_sync(mask, nh);
+      nd = __reduce_add_sync(mask, nd);
+      if ((threadIdx.x & 31) == 0) {
+        if (nh) atomicAdd(&a.counters[C_HLL], (unsigned long long)nh);
+        if (nd) atomicAdd(&a.counters[C_HLLD], (unsigned long long)nd);
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (nrho) atomicAdd(&a.counters[C_RHO_FLOOR], (unsigned long long)nrho);
+      if (np) atomicAdd(&a.counters[C_P_FLOOR], (unsigned long long)np);
+      if (anybad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+      if (StageTraits<STAGE>::last && sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
+    }
+  }
+
   // One work item: tile `item` (x fastest, then y, then z chunk) of one box.
   // Shared memory is the caller's dynamic allocation; every thread of the
   // CTA calls this with the same arguments.
@@ -654,6 +740,24 @@ struct StageKernel {
     bool bad = false;
     R smax = R(0);
 
+    if (g.n[2] == 1 && g.bc[2] == 0) {
+      // A two-dimensional box (one periodic z cell): every ring slot holds
+      // plane 0, so one flux pass (the z-faces, which feed E_x and E_y, and
+      // the x/y faces of the plane) replaces the chunk prologue and the
+      // first plane of the 3D march.
+      for (int m = -1; m <= 2; ++m) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, m, m == 0 || m == 1);
+      __syncthreads();
+      if (LEARN) fluxes_learned(g, a, sm, queue, qcnt, 0, 1, true, gi0, gj0, kb, ke, nh, nd);
+      else fluxes(g, sm, 0, 1, true);
+      __syncthreads();
+      edges_2d(g, sm);
+      __syncthreads();
+      new_faces(g, a, sm, NB, dt, gi0, gj0, 0, 0, 1);
+      __syncthreads();
+      new_cells(g, a, sm, NB, dt, gi0, gj0, 0, nrho, np, bad, smax);
+      finish(a, nrho, np, nh, nd, bad, smax);
+      return;
+    }
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 2, false);
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 1, true);
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb, true);
@@ -676,27 +780,7 @@ struct StageKernel {
       }
     }
 
-    const unsigned mask = 0xffffffffu;
-    nrho = __reduce_add_sync(mask, nrho);
-    np = __reduce_add_sync(mask, np);
-    const unsigned anybad = __any_sync(mask, bad);
-    double sm64 = (double)smax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sm64 = fmax(sm64, __shfl_xor_sync(mask, sm64, o));
-    if (LEARN) {
-      nh = __reduce_add_sync(mask, nh);
-      nd = __reduce_add_sync(mask, nd);
-      if ((threadIdx.x & 31) == 0) {
-        if (nh) atomicAdd(&a.counters[C_HLL], (unsigned long long)nh);
-        if (nd) atomicAdd(&a.counters[C_HLLD], (unsigned long long)nd);
-      }
-    }
-    if ((threadIdx.x & 31) == 0) {
-      if (nrho) atomicAdd(&a.counters[C_RHO_FLOOR], (unsigned long long)nrho);
-      if (np) atomicAdd(&a.counters[C_P_FLOOR], (unsigned long long)np);
-      if (anybad) atomicOr(a.status, (unsigned)ST_NONFINITE);
-      if (StageTraits<STAGE>::last && sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
-    }
+    finish(a, nrho, np, nh, nd, bad, smax);
   }
 };
 
