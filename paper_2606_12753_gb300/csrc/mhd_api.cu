@@ -23,6 +23,9 @@ cudaError_t set_smem_fp32(int, int, size_t);
 size_t smem_bytes_fp64(int, int);
 size_t smem_bytes_mixed(int, int);
 size_t smem_bytes_fp32(int, int);
+size_t smem_bytes_char_fp64();
+size_t smem_bytes_char_mixed();
+size_t smem_bytes_char_fp32();
 cudaError_t launch_stage_learned_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_stage_learned_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_stage_learned_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
@@ -119,6 +122,19 @@ size_t stage_smem_bytes(int prec, int tx, int ty) {
   }
 }
 bool stage_tile_supported(int prec, int tx, int ty) { return stage_smem_bytes(prec, tx, ty) > 0; }
+
+// Dynamic shared memory of the kernels a configuration launches: the
+// characteristic-reconstruction kernels also hold per-cell slopes.
+static size_t config_smem_bytes(int prec, int recon, int tx, int ty) {
+  if (recon == MHD_RECON_CHARACTERISTIC) {
+    switch (prec) {
+      case P_FP64: return smem_bytes_char_fp64();
+      case P_MIXED: return smem_bytes_char_mixed();
+      default: return smem_bytes_char_fp32();
+    }
+  }
+  return stage_smem_bytes(prec, tx, ty);
+}
 }  // namespace mhd
 
 using namespace mhd;
@@ -237,9 +253,9 @@ static int validate(const mhd_config* c, mhd_handle* h) {
   if (c->recon == MHD_RECON_CHARACTERISTIC &&
       (tx != 16 || ty != 8 || c->integrator != MHD_RK2 || c->riemann == MHD_LEARNED))
     return fail(h, MHD_ERR_INVALID, "characteristic reconstruction runs on the 16x8 tile with RK2 and HLLD or HLL");
-  if (stage_smem_bytes(c->precision, tx, ty) > 227 * 1024)
+  if (config_smem_bytes(c->precision, c->recon, tx, ty) > 227 * 1024)
     return fail(h, MHD_ERR_INVALID, "tile %dx%d needs %zu B of shared memory (> 227 KB)", tx, ty,
-                stage_smem_bytes(c->precision, tx, ty));
+                config_smem_bytes(c->precision, c->recon, tx, ty));
   return MHD_OK;
 }
 
@@ -290,7 +306,7 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   h->elem = cfg->precision == MHD_FP32 ? 4 : 8;
   h->kelem = cfg->precision == MHD_FP64 ? 8 : 4;
   h->welem = cfg->precision == MHD_FP64 ? 8 : 4;
-  h->smem_bytes = stage_smem_bytes(cfg->precision, h->geo.TX, h->geo.TY);
+  h->smem_bytes = config_smem_bytes(cfg->precision, cfg->recon, h->geo.TX, h->geo.TY);
   cudaError_t e = cudaGetDevice(&h->device);
   const size_t bytes = (size_t)h->geo.total * h->elem;
   const size_t kbytes = (size_t)h->geo.total * h->kelem;

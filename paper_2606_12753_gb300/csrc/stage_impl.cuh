@@ -55,14 +55,22 @@ struct Tile {
   static constexpr int nI = W + H + 4;
   // flux items of one plane: z-faces, x-faces, y-faces
   static constexpr int nItems = nZ + nX + nY;
+  // per-cell slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
+  // x and y slopes of the current plane, z slopes of two planes (by parity)
+  static constexpr int nSl = 7 * nZ;
+  static constexpr int nSlope = 4 * nSl;
   template <typename R, typename S>
-  static constexpr size_t bytes() {
+  __host__ __device__ static constexpr size_t core_bytes() {
     size_t b = (size_t)nRtot * sizeof(R);
     b = (b + 15) / 16 * 16;
     b += (size_t)nS * sizeof(S);
     b = (b + 15) / 16 * 16;
     b += (size_t)nI * sizeof(int);
-    return b;
+    return (b + 15) / 16 * 16;
+  }
+  template <typename R, typename S, bool SLOPES = false>
+  static constexpr size_t bytes() {
+    return core_bytes<R, S>() + (SLOPES ? (size_t)nSlope * sizeof(R) : 0);
   }
 };
 
@@ -137,10 +145,21 @@ __device__ void cell_prims(const Geo& g, const StageArgs& a, double dt, int i, i
 // learned HLL/HLLD switch, characteristic reconstruction.
 enum { FM_PLAIN = 0, FM_LEARNED = 1, FM_CHAR = 2 };
 
+// Whether a stage kernel computes each cell's slopes once per plane into
+// shared memory (a slope phase before the flux phase) instead of once per
+// face that uses it: FP64 on tiles of up to 128 columns (the FP64 pipe bounds
+// it and the slopes fit beside the ring without costing occupancy) and
+// characteristic reconstruction (an eigen-decomposition per slope).
+template <int PREC, int MODE, int TX, int TY>
+constexpr bool slopes_in_smem() {
+  return MODE == FM_CHAR || (PREC == P_FP64 && MODE == FM_PLAIN && TX * TY <= 128);
+}
+
 template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN>
 struct StageKernel {
   static constexpr bool LEARN = MODE == FM_LEARNED;
   static constexpr bool CHAR = MODE == FM_CHAR;
+  static constexpr bool SLOPES = slopes_in_smem<PREC, MODE, TX, TY>();
   using R = typename Prec<PREC>::R;
   using S = typename Prec<PREC>::S;
   using K = typename Prec<PREC>::K;
@@ -214,6 +233,113 @@ struct StageKernel {
       }
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
       plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+      if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
+      else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
+      store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
+    }
+    cell_emf(sm, q);
+  }
+
+  // ------------------------------------------------------------- phase B0
+  // Slopes of plane q's cells over the (TX+2) x (TY+2) grid the faces touch:
+  // x and y (for the x-, y-faces of plane q) and z (for the z-faces on both
+  // sides of plane q; kept by parity).  zonly: only the z slopes.
+  static __device__ __forceinline__ void slopes(const Geo& g, R* sm, R* sl, int q, bool zonly) {
+    const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
+    const R gam = (R)g.gamma;
+    constexpr int n = T::nZ;
+    const int first = zonly ? 2 * n : 0;
+    for (int it = first + threadIdx.x; it < 3 * n; it += blockDim.x) {
+      const int D = it / n, cidx = it - D * n;
+      const int i = cidx % (TX + 2) - 1, j = cidx / (TX + 2) - 1;
+      const int r = (i + 2) + W * (j + 2);
+      R c[3][7], out[7];
+      R bnc = R(0);
+      if (D == 0) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) gather<0>(Pq, T::nR, r - 1 + s, c[s]);
+        if (CHAR) bnc = Pq[5 * T::nR + r];
+      } else if (D == 1) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) gather<1>(Pq, T::nR, r + (s - 1) * W, c[s]);
+        if (CHAR) bnc = Pq[6 * T::nR + r];
+      } else {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) gather<2>(sm + T::oP + ((q - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
+        if (CHAR) bnc = Pq[7 * T::nR + r];
+      }
+      if (CHAR) {
+        char_slope(c[0], c[1], c[2], bnc, gam, out);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) out[v] = mc_slope(c[0][v], c[1][v], c[2][v]);
+      }
+      R* dst = D == 0 ? sl : (D == 1 ? sl + T::nSl : sl + (2 + (q & 1)) * T::nSl);
+#pragma unroll
+      for (int v = 0; v < 7; ++v) dst[v * n + cidx] = out[v];
+    }
+  }
+
+  // Phase B with the slopes of phase B0: per face item, the two cells across
+  // the face, their slopes, PLM values, Riemann flux.
+  static __device__ __forceinline__ void fluxes_sl(const Geo& g, R* sm, const R* sl, int k, int q, bool with_z) {
+    const int nZ = with_z ? T::nZ : 0;
+    const int nitems = nZ + T::nX + T::nY;
+    const R gam = (R)g.gamma;
+    const R ig = R(1) / (gam - R(1));
+    const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
+    const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
+    constexpr int n = T::nZ;
+    for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
+      R c1[7], c2[7], s1[7], s2[7], wl[7], wr[7], f[7], bn, cm;
+      int o, D, ia, ib;   // ia, ib: slope indices of the two cells
+      const R* sa;
+      const R* sb;
+      if (w < nZ) {
+        const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
+        const int r = (i + 2) + W * (j + 2);
+        gather<2>(sm + T::oP + (k & 3) * 8 * T::nR, T::nR, r, c1);
+        gather<2>(sm + T::oP + ((k + 1) & 3) * 8 * T::nR, T::nR, r, c2);
+        bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
+        ia = ib = w;
+        sa = sl + (2 + (k & 1)) * T::nSl;
+        sb = sl + (2 + ((k + 1) & 1)) * T::nSl;
+        o = w;
+        D = 2;
+      } else if (w < nZ + T::nX) {
+        o = w - nZ;
+        const int i = o % (TX + 1), j = o / (TX + 1) - 1;
+        const int r = (i + 2) + W * (j + 2);
+        gather<0>(Pq, T::nR, r - 1, c1);
+        gather<0>(Pq, T::nR, r, c2);
+        bn = BNq[r];
+        ia = i + (TX + 2) * (j + 1);
+        ib = ia + 1;
+        sa = sb = sl;
+        D = 0;
+      } else {
+        o = w - nZ - T::nX;
+        const int i = o % (TX + 2) - 1, j = o / (TX + 2);
+        const int r = (i + 2) + W * (j + 2);
+        gather<1>(Pq, T::nR, r - W, c1);
+        gather<1>(Pq, T::nR, r, c2);
+        bn = BNq[T::nR + r];
+        ib = (i + 1) + (TX + 2) * (j + 1);
+        ia = ib - (TX + 2);
+        sa = sb = sl + T::nSl;
+        D = 1;
+      }
+#pragma unroll
+      for (int v = 0; v < 7; ++v) {
+        s1[v] = sa[v * n + ia];
+        s2[v] = sb[v * n + ib];
+        wl[v] = c1[v] + R(0.5) * s1[v];
+        wr[v] = c2[v] - R(0.5) * s2[v];
+      }
+      wl[0] = rmax(wl[0], (R)g.rho_floor);
+      wr[0] = rmax(wr[0], (R)g.rho_floor);
+      wl[4] = rmax(wl[4], (R)g.p_floor);
+      wr[4] = rmax(wr[4], (R)g.p_floor);
       if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
       else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
@@ -712,6 +838,8 @@ struct StageKernel {
     // new_faces (the z-face part carries face k+1/2 over to the next plane)
     unsigned short* queue = reinterpret_cast<unsigned short*>(NB);
     static_assert((size_t)T::nItems * sizeof(unsigned short) <= (size_t)2 * T::nE * sizeof(S), "queue does not fit");
+    constexpr size_t sl_off = T::template core_bytes<R, S>();
+    R* sl = reinterpret_cast<R*>(smem_raw + sl_off);   // used when SLOPES
 
     int b = item;
     const int tile_x = b % g.ntx;
@@ -747,8 +875,16 @@ struct StageKernel {
       // first plane of the 3D march.
       for (int m = -1; m <= 2; ++m) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, m, m == 0 || m == 1);
       __syncthreads();
-      if (LEARN) fluxes_learned(g, a, sm, queue, qcnt, 0, 1, true, gi0, gj0, kb, ke, nh, nd);
-      else fluxes(g, sm, 0, 1, true);
+      if constexpr (SLOPES) {
+        slopes(g, sm, sl, 0, true);
+        slopes(g, sm, sl, 1, false);
+        __syncthreads();
+        fluxes_sl(g, sm, sl, 0, 1, true);
+      } else if constexpr (LEARN) {
+        fluxes_learned(g, a, sm, queue, qcnt, 0, 1, true, gi0, gj0, kb, ke, nh, nd);
+      } else {
+        fluxes(g, sm, 0, 1, true);
+      }
       __syncthreads();
       edges_2d(g, sm);
       __syncthreads();
@@ -762,14 +898,28 @@ struct StageKernel {
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 1, true);
     load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb, true);
     __syncthreads();
-    if (LEARN) fluxes_learned(g, a, sm, queue, qcnt, kb - 2, kb - 1, false, gi0, gj0, kb, ke, nh, nd);
-    else fluxes(g, sm, kb - 2, kb - 1, false);
+    if constexpr (SLOPES) {
+      slopes(g, sm, sl, kb - 1, false);
+      __syncthreads();
+      fluxes_sl(g, sm, sl, kb - 2, kb - 1, false);
+    } else if constexpr (LEARN) {
+      fluxes_learned(g, a, sm, queue, qcnt, kb - 2, kb - 1, false, gi0, gj0, kb, ke, nh, nd);
+    } else {
+      fluxes(g, sm, kb - 2, kb - 1, false);
+    }
     __syncthreads();
     for (int k = kb - 1; k < ke; ++k) {
       load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true);
       __syncthreads();
-      if (LEARN) fluxes_learned(g, a, sm, queue, qcnt, k, k + 1, true, gi0, gj0, kb, ke, nh, nd);
-      else fluxes(g, sm, k, k + 1, true);
+      if constexpr (SLOPES) {
+        slopes(g, sm, sl, k + 1, false);
+        __syncthreads();
+        fluxes_sl(g, sm, sl, k, k + 1, true);
+      } else if constexpr (LEARN) {
+        fluxes_learned(g, a, sm, queue, qcnt, k, k + 1, true, gi0, gj0, kb, ke, nh, nd);
+      } else {
+        fluxes(g, sm, k, k + 1, true);
+      }
       __syncthreads();
       divergence_and_edges(g, sm, k);
       __syncthreads();

@@ -37,11 +37,14 @@ size_t smem_bytes_mixed(int tx, int ty) {
   using R = Prec<P_MIXED>::R;
   using S = Prec<P_MIXED>::S;
 #define X(TXv, TYv) \
-  if (tx == TXv && ty == TYv) return Tile<TXv, TYv>::bytes<R, S>();
+  if (tx == TXv && ty == TYv) return Tile<TXv, TYv>::bytes<R, S, slopes_in_smem<P_MIXED, FM_PLAIN, TXv, TYv>()>();
   MHD_TILES(X)
 #undef X
   return 0;
 }
+
+// characteristic reconstruction (16 x 8 tile) keeps its slopes in shared memory
+size_t smem_bytes_char_mixed() { return Tile<16, 8>::bytes<Prec<P_MIXED>::R, Prec<P_MIXED>::S, true>(); }
 
 cudaError_t launch_prims_mixed(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
   prims_kernel<P_MIXED><<<nblocks, 256, 0, st>>>(g, args);
