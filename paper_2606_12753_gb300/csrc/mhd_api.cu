@@ -267,12 +267,19 @@ static void fill_geo(const mhd_config* c, Geo* g) {
     g->nf[a] = g->n[a] + (c->bc[a] == MHD_BC_OUTFLOW ? 1 : 0);
   }
   g->inv_d[0] = 1.0 / c->dx; g->inv_d[1] = 1.0 / c->dy; g->inv_d[2] = 1.0 / c->dz;
+  for (int a = 0; a < 3; ++a) g->finv_d[a] = (float)g->inv_d[a];
   g->gamma = c->gamma; g->rho_floor = c->rho_floor; g->p_floor = c->p_floor; g->cfl = c->cfl;
   g->emf_mean = c->emf == MHD_EMF_MEAN;
   g->riemann = c->riemann == MHD_HLL ? 1 : (c->riemann == MHD_LEARNED ? 2 : 0);
   g->recon = c->recon == MHD_RECON_CHARACTERISTIC ? 1 : 0;
   g->deadband = c->precision == MHD_FP64 ? 1e-10 : 1e-6;
   if (getenv("MHD_DEADBAND")) g->deadband = atof(getenv("MHD_DEADBAND"));
+  g->gm1 = g->gamma - 1.0;
+  g->fgamma = (float)g->gamma;
+  g->fgm1 = (float)g->gm1;
+  g->frho_floor = (float)g->rho_floor;
+  g->fp_floor = (float)g->p_floor;
+  g->fdeadband = (float)g->deadband;
   resolve_tile(c, &g->TX, &g->TY, &g->TZ);
   g->ntx = (g->n[0] + g->TX - 1) / g->TX;
   g->nty = (g->n[1] + g->TY - 1) / g->TY;

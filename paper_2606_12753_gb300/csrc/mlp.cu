@@ -271,8 +271,8 @@ __global__ void dump_faces_kernel(Geo g, const R* W, const long long* ids, long 
     }
     const R bn = W[(8 + d) * g.ncell + s];
     R wl[7], wr[7], fd[7], fl[7];
-    plm_face(cells[0], cells[1], cells[2], cells[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
-    const R gam = (R)g.gamma;
+    plm_face(cells[0], cells[1], cells[2], cells[3], wl, wr, gpar<R>(g.rho_floor, g.frho_floor), gpar<R>(g.p_floor, g.fp_floor));
+    const R gam = gpar<R>(g.gamma, g.fgamma);
     const R cl = fast_speed(wl, bn, gam), cr = fast_speed(wr, bn, gam);
     hlld_flux(wl, wr, bn, gam, fd);
     hll_flux(wl, wr, bn, gam, fl);

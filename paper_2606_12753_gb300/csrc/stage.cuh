@@ -45,6 +45,11 @@ struct Geo {
   int bc[3];       // 0 periodic, 1 outflow
   double inv_d[3];
   double gamma, rho_floor, p_floor, cfl;
+  double gm1;      // gamma - 1
+  // the same constants rounded to FP32 (host-side), for the FP32 arithmetic
+  // of the mixed and FP32 forms: a conversion in the kernel would run on the
+  // FP64 pipe
+  float fgamma, fgm1, frho_floor, fp_floor, fdeadband, finv_d[3];
   int emf_mean;
   int riemann;     // 0 HLLD, 1 HLL, 2 learned
   int recon;       // 0 MC on the primitives, 1 MC on the characteristic variables
@@ -82,6 +87,47 @@ struct StageArgs {
   unsigned char* choices;   // learned switch, stage 1: per owned face 1 = HLLD, 0 = HLL (or null)
   float* logits;            // ... and the network's logit (or null)
 };
+
+// A physical constant in the arithmetic type R (FP64 value, or its host-side
+// FP32 rounding).
+template <typename R> __device__ __forceinline__ R gpar(double d, float f);
+template <> __device__ __forceinline__ double gpar<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float gpar<float>(double, float f) { return f; }
+
+// Exact conversions between binary32 and binary64 on the integer pipes (the
+// hardware conversions run on the FP64 pipe, which on this part issues one
+// warp-instruction per ~17 SM cycles and bounds the mixed form).  Field
+// layouts of IEEE 754-2008: binary32 = sign | 8-bit exponent (bias 127) |
+// 23-bit fraction, binary64 = sign | 11-bit exponent (bias 1023) | 52-bit
+// fraction; the biases differ by 896.
+// widen: binary32 -> binary64, exact; zero and normal numbers by moving the
+// fields, subnormal/inf/NaN inputs by the hardware conversion.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned m = b & 0x7fffffffu;
+  if (m - 0x00800000u >= 0x7f000000u && m != 0u) return (double)x;
+  const unsigned hi = m == 0u ? b : (b & 0x80000000u) | ((m >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+// narrow: binary64 -> binary32 rounded to nearest, ties to even.  Inputs whose
+// result is a normal binary32 (2^-126 <= |x| < 2^128 before rounding;
+// rounding up past the largest finite value gives inf, as required) drop the
+// 29 low fraction bits and round on them; zero keeps its sign; everything
+// else (subnormal results, overflow, inf, NaN) takes the hardware conversion.
+__device__ __forceinline__ float narrow(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned m = hi & 0x7fffffffu;
+  if (m - 0x38100000u >= 0x47f00000u - 0x38100000u) {
+    if ((m | lo) == 0u) return __uint_as_float(hi);
+    return __double2float_rn(x);
+  }
+  unsigned r = ((m - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  r += (rest > 0x10000000u) | ((rest == 0x10000000u) & r);
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+__device__ __forceinline__ double to_f64(float x) { return widen(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
 
 __host__ __device__ inline int wrapc(int i, int n, int bc) {
   if (bc == 0) {
@@ -123,20 +169,23 @@ __device__ __forceinline__ void recover(const Geo& g, double rho, double mx, dou
   const double bb = sx * sx + sy * sy + sz * sz;
   if (PREC == P_FP64) {
     const double rinv = 1.0 / rho;
-    double p = (g.gamma - 1.0) * (e - 0.5 * mm * rinv - 0.125 * bb);
+    double p = g.gm1 * (e - 0.5 * mm * rinv - 0.125 * bb);
     p_hit = p < g.p_floor;
     if (p_hit) p = g.p_floor;
     w[0] = (R)rho; w[1] = (R)(mx * rinv); w[2] = (R)(my * rinv); w[3] = (R)(mz * rinv); w[4] = (R)p;
     w[5] = (R)(0.5 * sx); w[6] = (R)(0.5 * sy); w[7] = (R)(0.5 * sz);
   } else {
-    const float rf = 1.0f / (float)rho;
-    const double r0 = (double)rf;
+    const float rho_f = narrow(rho);
+    const float rf = 1.0f / rho_f;
+    const double r0 = widen(rf);
     const double r1 = fma(r0, fma(-rho, r0, 1.0), r0);
-    double p = (g.gamma - 1.0) * (e - 0.5 * mm * r1 - 0.125 * bb);
+    double p = g.gm1 * (e - 0.5 * mm * r1 - 0.125 * bb);
     p_hit = p < g.p_floor;
     if (p_hit) p = g.p_floor;
-    w[0] = (R)rho; w[1] = (R)mx * rf; w[2] = (R)my * rf; w[3] = (R)mz * rf; w[4] = (R)p;
-    w[5] = 0.5f * (R)sx; w[6] = 0.5f * (R)sy; w[7] = 0.5f * (R)sz;
+    w[0] = rho_f; w[1] = narrow(mx) * rf; w[2] = narrow(my) * rf; w[3] = narrow(mz) * rf; w[4] = narrow(p);
+    w[5] = 0.5f * narrow(sx); w[6] = 0.5f * narrow(sy); w[7] = 0.5f * narrow(sz);
+    w[8] = narrow(bxl); w[9] = narrow(byl); w[10] = narrow(bzl);
+    return;
   }
   w[8] = (R)bxl; w[9] = (R)byl; w[10] = (R)bzl;
 }
@@ -147,16 +196,16 @@ __device__ __forceinline__ void recover<P_FP32>(const Geo& g, double rho, double
                                                 double bxl, double bxh, double byl, double byh, double bzl,
                                                 double bzh, float* w, int& rho_hit, int& p_hit) {
   float r = (float)rho;
-  rho_hit = r < (float)g.rho_floor;
-  if (rho_hit) r = (float)g.rho_floor;
+  rho_hit = r < g.frho_floor;
+  if (rho_hit) r = g.frho_floor;
   const float rinv = 1.0f / r;
   const float fx = (float)mx, fy = (float)my, fz = (float)mz;
   const float bx = 0.5f * ((float)bxl + (float)bxh), by = 0.5f * ((float)byl + (float)byh),
               bz = 0.5f * ((float)bzl + (float)bzh);
-  float p = (float)(g.gamma - 1.0) * ((float)e - 0.5f * (fx * fx + fy * fy + fz * fz) * rinv -
+  float p = g.fgm1 * ((float)e - 0.5f * (fx * fx + fy * fy + fz * fz) * rinv -
                                       0.5f * (bx * bx + by * by + bz * bz));
-  p_hit = p < (float)g.p_floor;
-  if (p_hit) p = (float)g.p_floor;
+  p_hit = p < g.fp_floor;
+  if (p_hit) p = g.fp_floor;
   w[0] = r; w[1] = fx * rinv; w[2] = fy * rinv; w[3] = fz * rinv; w[4] = p;
   w[5] = bx; w[6] = by; w[7] = bz;
   w[8] = (float)bxl; w[9] = (float)byl; w[10] = (float)bzl;
@@ -172,8 +221,8 @@ __device__ __forceinline__ R cfl_speed(const Geo& g, const R* w) {
     if (g.n[d] > 1) {
       const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
       R q[7] = {w[0], w[1 + d], w[1 + t1], w[1 + t2], w[4], w[5 + t1], w[5 + t2]};
-      const R cf = fast_speed(q, w[5 + d], (R)g.gamma);
-      sum += (rabs(q[1]) + cf) * (R)g.inv_d[d];
+      const R cf = fast_speed(q, w[5 + d], gpar<R>(g.gamma, g.fgamma));
+      sum += (rabs(q[1]) + cf) * gpar<R>(g.inv_d[d], g.finv_d[d]);
     }
   }
   return sum;

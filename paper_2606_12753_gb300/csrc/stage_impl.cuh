@@ -52,7 +52,7 @@ struct Tile {
   static constexpr int nS = 2 * nE + 2 * nC;
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
-  static constexpr int nI = W + H + 4;
+  static constexpr int nI = W + H + 6;   // column/row maps, switch counters, the stage's dt
   // flux items of one plane: z-faces, x-faces, y-faces
   static constexpr int nItems = nZ + nX + nY;
   // per-cell slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
@@ -141,6 +141,13 @@ __device__ void cell_prims(const Geo& g, const StageArgs& a, double dt, int i, i
   recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], bxl, bxh, byl, byh, bzl, bzh, w, rho_hit, p_hit);
 }
 
+// Step size of a stage in the forms its updates use: dt and dt/2 in FP64 and
+// rounded to FP32.
+struct StepDt {
+  double dt, hdt;
+  float fdt, fhdt;
+};
+
 // Flux modes of the stage kernel: plain (HLLD or HLL by Geo::riemann), the
 // learned HLL/HLLD switch, characteristic reconstruction.
 enum { FM_PLAIN = 0, FM_LEARNED = 1, FM_CHAR = 2 };
@@ -217,7 +224,7 @@ struct StageKernel {
   static __device__ __forceinline__ void fluxes(const Geo& g, R* sm, int k, int q, bool with_z) {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
-    const R gam = (R)g.gamma;
+    const R gam = gpar<R>(g.gamma, g.fgamma);
     const R ig = R(1) / (gam - R(1));
     for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
       R c[4][7], wl[7], wr[7], f[7], bn, cm;
@@ -225,14 +232,14 @@ struct StageKernel {
       if (CHAR) {
         R bnc[2];
         const int D = item_stencil(sm, k, q, nZ, w, c, bn, o, bnc);
-        plm_face_char(c[0], c[1], c[2], c[3], bnc[0], bnc[1], gam, wl, wr, (R)g.rho_floor, (R)g.p_floor);
+        plm_face_char(c[0], c[1], c[2], c[3], bnc[0], bnc[1], gam, wl, wr, gpar<R>(g.rho_floor, g.frho_floor), gpar<R>(g.p_floor, g.fp_floor));
         if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
         else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
         store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
         continue;
       }
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
-      plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+      plm_face(c[0], c[1], c[2], c[3], wl, wr, gpar<R>(g.rho_floor, g.frho_floor), gpar<R>(g.p_floor, g.fp_floor));
       if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
       else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
@@ -246,7 +253,7 @@ struct StageKernel {
   // sides of plane q; kept by parity).  zonly: only the z slopes.
   static __device__ __forceinline__ void slopes(const Geo& g, R* sm, R* sl, int q, bool zonly) {
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
-    const R gam = (R)g.gamma;
+    const R gam = gpar<R>(g.gamma, g.fgamma);
     constexpr int n = T::nZ;
     const int first = zonly ? 2 * n : 0;
     for (int it = first + threadIdx.x; it < 3 * n; it += blockDim.x) {
@@ -285,7 +292,7 @@ struct StageKernel {
   static __device__ __forceinline__ void fluxes_sl(const Geo& g, R* sm, const R* sl, int k, int q, bool with_z) {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
-    const R gam = (R)g.gamma;
+    const R gam = gpar<R>(g.gamma, g.fgamma);
     const R ig = R(1) / (gam - R(1));
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
     const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
@@ -336,10 +343,10 @@ struct StageKernel {
         wl[v] = c1[v] + R(0.5) * s1[v];
         wr[v] = c2[v] - R(0.5) * s2[v];
       }
-      wl[0] = rmax(wl[0], (R)g.rho_floor);
-      wr[0] = rmax(wr[0], (R)g.rho_floor);
-      wl[4] = rmax(wl[4], (R)g.p_floor);
-      wr[4] = rmax(wr[4], (R)g.p_floor);
+      wl[0] = rmax(wl[0], gpar<R>(g.rho_floor, g.frho_floor));
+      wr[0] = rmax(wr[0], gpar<R>(g.rho_floor, g.frho_floor));
+      wl[4] = rmax(wl[4], gpar<R>(g.p_floor, g.fp_floor));
+      wr[4] = rmax(wr[4], gpar<R>(g.p_floor, g.fp_floor));
       if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
       else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
@@ -430,7 +437,7 @@ struct StageKernel {
     H[4 * n + o] = f[4];
     C[o] = -f[5];
     C[n + o] = f[6];
-    C[2 * n + o] = oriented_mass_flux(f[0], rl, rr, cm, (R)g.deadband);
+    C[2 * n + o] = oriented_mass_flux(f[0], rl, rr, cm, gpar<R>(g.deadband, g.fdeadband));
   }
   static __device__ __forceinline__ void store_any(int D, const Geo& g, R* sm, int q, int o, const R* f, R cm, R rl,
                                                    R rr) {
@@ -459,7 +466,7 @@ struct StageKernel {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
     const int lane = threadIdx.x & 31;
-    const R gam = (R)g.gamma;
+    const R gam = gpar<R>(g.gamma, g.fgamma);
     const float* master = a.mlp;
     const uint16_t* wb =
         reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(a.mlp) + MLP_MASTER_BYTES);
@@ -474,7 +481,7 @@ struct StageKernel {
       if (valid) {
         R c[4][7], wl[7], wr[7], bn;
         D = item_stencil(sm, k, q, nZ, w, c, bn, o);
-        plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+        plm_face(c[0], c[1], c[2], c[3], wl, wr, gpar<R>(g.rho_floor, g.frho_floor), gpar<R>(g.p_floor, g.fp_floor));
         face_features<R>(wl, wr, bn, fast_speed(wl, bn, gam), fast_speed(wr, bn, gam), feat);
       } else {
 #pragma unroll
@@ -515,7 +522,7 @@ struct StageKernel {
       R c[4][7], wl[7], wr[7], f[7], bn, cm;
       int o;
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
-      plm_face(c[0], c[1], c[2], c[3], wl, wr, (R)g.rho_floor, (R)g.p_floor);
+      plm_face(c[0], c[1], c[2], c[3], wl, wr, gpar<R>(g.rho_floor, g.frho_floor), gpar<R>(g.p_floor, g.fp_floor));
       if (t < nhll) {
         hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
         ++nh;
@@ -530,7 +537,7 @@ struct StageKernel {
 
   // ---------------------------------------------------------------- phase C
   static __device__ __forceinline__ void divergence_and_edges(const Geo& g, R* sm, int k) {
-    const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1], idz = (R)g.inv_d[2];
+    const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]), idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
     const int sk = k & 1, sk1 = (k + 1) & 1;
     R* DUk = sm + T::oDU + sk * 5 * T::nC;
     R* DUk1 = sm + T::oDU + sk1 * 5 * T::nC;
@@ -594,7 +601,7 @@ struct StageKernel {
   // their difference (exactly zero), and the edges E_x, E_y at k-1/2 and
   // k+1/2 are one set, written to both slots.
   static __device__ __forceinline__ void edges_2d(const Geo& g, R* sm) {
-    const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1];
+    const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]);
     R* DU0 = sm + T::oDU;
     const R* HX = sm + T::oHX;
     const R* HY = sm + T::oHY;
@@ -652,32 +659,32 @@ struct StageKernel {
   // RK2 stage 1 U* = U^n + dt K1 (K1 = l rounded to K), stage 2 U^n + dt/2 (K1 + l);
   // RK3 (input state U_in): U1 = U_in + dt l, U2 = 3/4 U^n + 1/4 (U_in + dt l),
   // U^{n+1} = 1/3 U^n + 2/3 (U_in + dt l)
-  static __device__ __forceinline__ S advance(const StageArgs& a, long long gidx, R l, double dt) {
+  static __device__ __forceinline__ S advance(const StageArgs& a, long long gidx, R l, const StepDt& t) {
     if (StageTraits<STAGE>::rk3) {
       const S ui = ((const S*)a.Uin)[gidx];
       if (PREC == P_FP32) {
-        const float e = ui + (float)dt * l;
+        const float e = ui + t.fdt * l;
         if (STAGE == ST_RK3_1) return e;
         const float un = ((const S*)a.U)[gidx];
         if (STAGE == ST_RK3_2) return 0.75f * un + 0.25f * e;
         return un / 3.0f + 2.0f / 3.0f * e;
       }
-      const double e = fma(dt, (double)l, (double)ui);
+      const double e = fma(t.dt, to_f64(l), (double)ui);
       if (STAGE == ST_RK3_1) return (S)e;
       const double un = (double)((const S*)a.U)[gidx];
       if (STAGE == ST_RK3_2) return (S)(0.75 * un + 0.25 * e);
-      return (S)(un / 3.0 + 2.0 / 3.0 * e);
+      return (S)((1.0 / 3.0) * un + (2.0 / 3.0) * e);
     }
     const S un = ((const S*)a.U)[gidx];
     if (STAGE == 1) {
       const K k1 = (K)l;
-      if (PREC == P_FP32) return un + (float)dt * k1;
-      return (S)fma(dt, (double)k1, (double)un);
+      if (PREC == P_FP32) return un + t.fdt * k1;
+      return (S)fma(t.dt, to_f64(k1), (double)un);
     } else {
       const K k1 = ((const K*)a.K1)[gidx];
-      if (PREC == P_FP32) return un + (float)(0.5 * dt) * (k1 + (float)l);
-      if (PREC == P_MIXED) return fma(0.5 * dt, (double)(k1 + (float)l), (double)un);
-      return (S)((double)un + 0.5 * dt * ((double)k1 + (double)l));
+      if (PREC == P_FP32) return un + t.fhdt * (k1 + l);
+      if (PREC == P_MIXED) return fma(t.hdt, to_f64(k1 + l), (double)un);
+      return (S)((double)un + t.hdt * ((double)k1 + (double)l));
     }
   }
 
@@ -697,9 +704,9 @@ struct StageKernel {
   }
 
   // ---------------------------------------------------------------- phase D
-  static __device__ __forceinline__ void new_faces(const Geo& g, const StageArgs& a, R* sm, S* NB, double dt,
+  static __device__ __forceinline__ void new_faces(const Geo& g, const StageArgs& a, R* sm, S* NB, const StepDt& dt,
                                                    int gi0, int gj0, int k, int kb, int ke) {
-    const R idx = (R)g.inv_d[0], idy = (R)g.inv_d[1], idz = (R)g.inv_d[2];
+    const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]), idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
     const R* EZ = sm + T::oEZ;
     const R* EX0 = sm + T::oEXY + (k & 1) * 2 * T::nE;   // k-1/2
     const R* EY0 = EX0 + T::nE;
@@ -755,7 +762,8 @@ struct StageKernel {
     }
   }
 
-  static __device__ __forceinline__ void new_cells(const Geo& g, const StageArgs& a, R* sm, const S* NB, double dt,
+  static __device__ __forceinline__ void new_cells(const Geo& g, const StageArgs& a, R* sm, const S* NB,
+                                                   const StepDt& dt,
                                                    int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
                                                    bool& bad, R& smax) {
     const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
@@ -851,18 +859,27 @@ struct StageKernel {
     const int ke = min(kb + g.TZ, g.n[2]);
 
     if (StageTraits<STAGE>::first && item == 0 && threadIdx.x == 0) *a.nextword = 0ull;
-    double dt = a.dt;
-    if (!(dt > 0.0)) {
-      const double m = __longlong_as_double((long long)*a.dtword);
-      dt = m > 0.0 ? g.cfl / m : 0.0;
-    }
     __syncthreads();   // the previous item of this CTA may still read the tables
     for (int t = threadIdx.x; t < T::W + T::H; t += blockDim.x) {
       if (t < T::W) colc[t] = wrapc(gi0 - 2 + t, g.n[0], g.bc[0]);
       else rowc[t - T::W] = wrapc(gj0 - 2 + (t - T::W), g.n[1], g.bc[1]);
     }
     if (LEARN && threadIdx.x < 4) qcnt[threadIdx.x] = 0;
+    // the stage's dt: explicit, or cfl / (CFL max of the step's start), one
+    // FP64 division per CTA
+    int* dtw = qcnt + 4;
+    if (threadIdx.x == 0) {
+      double d = a.dt;
+      if (!(d > 0.0)) {
+        const double m = __longlong_as_double((long long)*a.dtword);
+        d = m > 0.0 ? g.cfl / m : 0.0;
+      }
+      dtw[0] = __double2hiint(d);
+      dtw[1] = __double2loint(d);
+    }
     __syncthreads();
+    const double dt = __hiloint2double(dtw[0], dtw[1]);
+    const StepDt sdt{dt, 0.5 * dt, narrow(dt), narrow(0.5 * dt)};
 
     unsigned nrho = 0, np = 0, nh = 0, nd = 0;
     bool bad = false;
@@ -888,9 +905,9 @@ struct StageKernel {
       __syncthreads();
       edges_2d(g, sm);
       __syncthreads();
-      new_faces(g, a, sm, NB, dt, gi0, gj0, 0, 0, 1);
+      new_faces(g, a, sm, NB, sdt, gi0, gj0, 0, 0, 1);
       __syncthreads();
-      new_cells(g, a, sm, NB, dt, gi0, gj0, 0, nrho, np, bad, smax);
+      new_cells(g, a, sm, NB, sdt, gi0, gj0, 0, nrho, np, bad, smax);
       finish(a, nrho, np, nh, nd, bad, smax);
       return;
     }
@@ -924,9 +941,9 @@ struct StageKernel {
       divergence_and_edges(g, sm, k);
       __syncthreads();
       if (k >= kb) {
-        new_faces(g, a, sm, NB, dt, gi0, gj0, k, kb, ke);
+        new_faces(g, a, sm, NB, sdt, gi0, gj0, k, kb, ke);
         __syncthreads();
-        new_cells(g, a, sm, NB, dt, gi0, gj0, k, nrho, np, bad, smax);
+        new_cells(g, a, sm, NB, sdt, gi0, gj0, k, nrho, np, bad, smax);
       }
     }
 
