@@ -41,6 +41,27 @@ STAGE_BYTES_RK3 = {"fp64": (304, 368, 368), "mixed": (216, 280, 280), "fp32": (1
 PAPER_OT352 = {"time_10_steps_s": 13.9, "hardware": "NVIDIA A100 64 GB (Leonardo), NVHPC 24.5 OpenACC, managed memory",
                "note": "total time of 10 steps of the paper's 3D Orszag-Tang test (Sec. 4, its figure of total "
                        "execution time); other hardware and a whole-application time: context only"}
+# Algorithmic flops per cell-update (one full step with its CFL maximum),
+# counted by the operation-counting build of the oracle on 32^3 patterns of
+# each workload's start state (oracle/opcount_table.py writes the table these
+# figures are copied from; a CPU test keeps the two equal).  "fp64" is the part
+# the mixed form computes in FP64 (primitive recoveries, RK accumulation), the
+# rest is FP32 there; the FP64 form computes all of it in FP64.
+FLOPS = {
+    ("turbulence", "primitive", "rk2"): {"total": 3438.012, "fp64_in_mixed": 112.0},
+    ("turbulence", "characteristic", "rk2"): {"total": 10301.774, "fp64_in_mixed": 112.0},
+    ("orszag_tang", "primitive", "rk2"): {"total": 3293.019, "fp64_in_mixed": 112.0},
+    ("orszag_tang", "primitive", "rk3"): {"total": 4934.793, "fp64_in_mixed": 192.0},
+}
+# the learned switch's network per face: 2 (16*32 + 32*32 + 32) flops, on the
+# lower x-, y- and z-faces of every cell in both stages
+MLP_FLOPS_PER_FACE = 2 * (16 * 32 + 32 * 32 + 32)
+# nominal arithmetic peaks from unit counts and the maximum SM clock: 152 SMs
+# x 2070 MHz x (2 FP64 FMA lanes per SM per clock, 128 FP32 FMA lanes) x 2
+# flops per FMA (the FP64 figure is GB300's 1.25 TFLOP/s FP64 rating)
+SMS, SM_MAX_GHZ = 152, 2.070
+FP64_NOMINAL_TFLOPS = SMS * SM_MAX_GHZ * 2 * 2 / 1e3
+FP32_NOMINAL_TFLOPS = SMS * SM_MAX_GHZ * 128 * 2 / 1e3
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -89,6 +110,40 @@ def job_rate(cells_per_rank: int, steps: int, ms_max: float, world: int) -> floa
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def flop_counts(args, box):
+    """Algorithmic flops per cell-update of this run's workload, or None
+    (uncounted workloads; the learned switch, whose HLL/HLLD mix varies)."""
+    if args.workload == "turbulence256_learned":
+        return None
+    kind = "turbulence" if box.name.startswith("turbulence") else (
+        "orszag_tang" if box.name.startswith("orszag_tang_3d") else None)
+    key = (kind, args.recon, "rk3" if args.workload == "ot3d352_rk3" else "rk2")
+    return FLOPS.get(key)
+
+
+def pipe_report(args, box, value_mcells, measured):
+    """FP64 and FP32 arithmetic rates of the run (algorithmic flops x
+    cell-updates/s) against the nominal and the measured pipe peaks."""
+    fl = flop_counts(args, box)
+    if fl is None:
+        return None
+    if args.precision == "fp64":
+        f64, f32 = fl["total"], 0.0
+    elif args.precision == "mixed":
+        f64, f32 = fl["fp64_in_mixed"], fl["total"] - fl["fp64_in_mixed"]
+    else:
+        f64, f32 = 0.0, fl["total"]
+    rate = value_mcells * 1e6
+    rep = {"flops_per_cell_update": fl["total"], "source": "operation-counting build of the oracle"}
+    for name, fpc, nom, meas in (("fp64", f64, FP64_NOMINAL_TFLOPS, measured.get("fp64_fma_tflops")),
+                                 ("fp32", f32, FP32_NOMINAL_TFLOPS, measured.get("fp32_fma_tflops"))):
+        ach = rate * fpc / 1e12
+        rep[name] = {"flops_per_cell_update": fpc, "achieved_tflops": ach, "peak_tflops": nom,
+                     "frac": ach / nom, "measured_peak_tflops": meas,
+                     "frac_of_measured": ach / meas if meas else None}
+    return rep
 
 
 def peaks():
@@ -368,6 +423,7 @@ def run_ours(args):
     ms_total = max_over_ranks(ms_total, world)
     value = job_rate(box.ncell, args.steps, ms_total, world)
 
+    measured = mhd.mhd_measure_pipe_peaks(stream.cuda_stream)
     peak, peak_kind = peaks()
     nst = len(stage_bytes)
     k = max(range(nst), key=lambda i: stage_ms[i] / max(launches[i], 1))
@@ -398,6 +454,28 @@ def run_ours(args):
         "stage_ms_per_launch": [stage_ms[i] / max(launches[i], 1) for i in range(nst)],
         "gpu_launches": nst * args.steps,
     }
+    out["pipes"] = pipe_report(args, box, value / world, measured)
+    if out["pipes"] is not None:
+        out["pipes"]["measured_peaks"] = measured
+    if args.precision == "fp64" and out["pipes"] is not None:
+        # the FP64 form is bound by its FP64 pipe: its roofline is arithmetic,
+        # the algorithmic flops of an average stage launch over the mean stage
+        # launch time, against the nominal FP64 peak
+        mean_ms = sum(stage_ms[i] / max(launches[i], 1) for i in range(nst)) / nst
+        fl = out["pipes"]["flops_per_cell_update"] * box.ncell / nst
+        ach = fl / (mean_ms / 1e3) / 1e12
+        out["roofline_hbm"] = out["roofline"]
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                           "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": traffic, "kernel": tag,
+                           "peak_kind": "nominal (152 SMs x 2070 MHz x 2 FP64 FMA lanes x 2 flops)",
+                           "measured_peak": measured["fp64_fma_tflops"],
+                           "frac_of_measured": ach / measured["fp64_fma_tflops"],
+                           "flops_per_launch": fl}
+    if learned:
+        mlp = 6 * MLP_FLOPS_PER_FACE * value / world * 1e6 / 1e12
+        out["pipes_tensor"] = {"mlp_flops_per_cell_update": 6 * MLP_FLOPS_PER_FACE, "achieved_tflops": mlp,
+                               "mma_sync_measured_peak_tflops": measured["bf16_mma_sync_tflops"],
+                               "frac_of_mma_sync": mlp / measured["bf16_mma_sync_tflops"]}
     if rk3:
         out["config"]["integrator"] = "SSP-RK3 (3 stage launches per step)"
         out["time_10_steps_s"] = 10 * ms_total / args.steps / 1e3

@@ -301,6 +301,27 @@ int mhd_batch_get_stats(mhd_batch* b, mhd_stats* out);
 void mhd_batch_destroy(mhd_batch* b);
 const char* mhd_batch_last_error(const mhd_batch* b);
 
+/* ---- arithmetic-pipe peaks --------------------------------------------
+ * Peak rates of the current device's arithmetic pipes, measured with
+ * dependent instruction chains (8 independent chains per thread, 8 CTAs of
+ * 256 threads per SM): FP64 FMA, FP32 FMA (an FMA counts 2 flops) and the
+ * BF16 tensor-core mma.sync m16n8k16 with FP32 accumulation that the learned
+ * face switch issues (4096 flops each).  They are the denominators of the
+ * arithmetic rooflines: the FP64 form's Godunov step (Sec. 2.2) is bound by
+ * its FP64 pipe, and the switch's network (an extension of the Riemann step,
+ * not in the paper) runs on the tensor pipe.
+ * Runs on cuda_stream (NULL: the default stream) and synchronises it; takes
+ * a few milliseconds and allocates a scratch buffer of 8 CTAs x 256 doubles
+ * per SM for its duration.  Errors: MHD_ERR_INVALID (null out), MHD_ERR_CUDA
+ * (text in mhd_last_error(NULL)). */
+typedef struct {
+  double fp64_fma_tflops;
+  double fp32_fma_tflops;
+  double bf16_mma_sync_tflops;
+  double ms[3];            /* measured time per launch of the three kernels */
+} mhd_pipe_peaks;
+int mhd_measure_pipe_peaks(void* cuda_stream, mhd_pipe_peaks* out);
+
 /* Free every resource of the handle (NULL is a no-op). */
 void mhd_destroy(mhd_handle* h);
 

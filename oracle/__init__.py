@@ -120,43 +120,48 @@ _P = C.POINTER(C.c_double)
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        L.orc_mc_slope.restype = C.c_double
-        L.orc_mc_slope.argtypes = [C.c_double] * 3
-        L.orc_fast_speed.restype = C.c_double
-        L.orc_fast_speed.argtypes = [_P, C.c_double, C.c_double]
-        for name in ("orc_phys_flux", "orc_hll", "orc_hlld"):
-            fn = getattr(L, name)
-            fn.restype = None
-        L.orc_phys_flux.argtypes = [_P, C.c_double, C.c_double, _P]
-        L.orc_hll.argtypes = [_P, _P, C.c_double, C.c_double, _P]
-        L.orc_hlld.argtypes = [_P, _P, C.c_double, C.c_double, _P]
-        PP = _P * 5
-        PF = _P * 3
-        L.orc_step.restype = None
-        L.orc_step.argtypes = [C.POINTER(_Cfg), PP, PF, C.c_double, C.POINTER(_Stats)]
-        L.orc_step_rk3.restype = None
-        L.orc_step_rk3.argtypes = [C.POINTER(_Cfg), PP, PF, C.c_double, C.POINTER(_Stats)]
-        L.orc_rhs.restype = None
-        L.orc_rhs.argtypes = [C.POINTER(_Cfg), PP, PF, PP, PF, C.POINTER(_Stats)]
-        L.orc_cfl_dt.restype = C.c_double
-        L.orc_cfl_dt.argtypes = [C.POINTER(_Cfg), PP, PF]
-        L.orc_divb_max.restype = C.c_double
-        L.orc_divb_max.argtypes = [C.POINTER(_Cfg), PF]
-        L.orc_bf16.restype = C.c_double
-        L.orc_bf16.argtypes = [C.c_double]
-        L.orc_features.restype = None
-        L.orc_features.argtypes = [_P, _P, C.c_double, C.c_double, _P]
-        L.orc_mlp_logit.restype = C.c_double
-        L.orc_mlp_logit.argtypes = [_P, _P]
-        L.orc_char_eig.restype = None
-        L.orc_char_eig.argtypes = [_P, C.c_double, C.c_double, _P, _P, _P]
-        L.orc_char_slope.restype = None
-        L.orc_char_slope.argtypes = [_P, _P, _P, C.c_double, C.c_double, _P]
-        L.orc_switch_logits.restype = None
-        L.orc_switch_logits.argtypes = [C.POINTER(_Cfg), PP, PF, _P]
-        _lib = L
+        _lib = bind(C.CDLL(build()))
     return _lib
+
+
+def bind(L):
+    """Declare the oracle's C signatures on a loaded library (the oracle, or
+    its operation-counting build, which exports the same functions)."""
+    L.orc_mc_slope.restype = C.c_double
+    L.orc_mc_slope.argtypes = [C.c_double] * 3
+    L.orc_fast_speed.restype = C.c_double
+    L.orc_fast_speed.argtypes = [_P, C.c_double, C.c_double]
+    for name in ("orc_phys_flux", "orc_hll", "orc_hlld"):
+        fn = getattr(L, name)
+        fn.restype = None
+    L.orc_phys_flux.argtypes = [_P, C.c_double, C.c_double, _P]
+    L.orc_hll.argtypes = [_P, _P, C.c_double, C.c_double, _P]
+    L.orc_hlld.argtypes = [_P, _P, C.c_double, C.c_double, _P]
+    PP = _P * 5
+    PF = _P * 3
+    L.orc_step.restype = None
+    L.orc_step.argtypes = [C.POINTER(_Cfg), PP, PF, C.c_double, C.POINTER(_Stats)]
+    L.orc_step_rk3.restype = None
+    L.orc_step_rk3.argtypes = [C.POINTER(_Cfg), PP, PF, C.c_double, C.POINTER(_Stats)]
+    L.orc_rhs.restype = None
+    L.orc_rhs.argtypes = [C.POINTER(_Cfg), PP, PF, PP, PF, C.POINTER(_Stats)]
+    L.orc_cfl_dt.restype = C.c_double
+    L.orc_cfl_dt.argtypes = [C.POINTER(_Cfg), PP, PF]
+    L.orc_divb_max.restype = C.c_double
+    L.orc_divb_max.argtypes = [C.POINTER(_Cfg), PF]
+    L.orc_bf16.restype = C.c_double
+    L.orc_bf16.argtypes = [C.c_double]
+    L.orc_features.restype = None
+    L.orc_features.argtypes = [_P, _P, C.c_double, C.c_double, _P]
+    L.orc_mlp_logit.restype = C.c_double
+    L.orc_mlp_logit.argtypes = [_P, _P]
+    L.orc_char_eig.restype = None
+    L.orc_char_eig.argtypes = [_P, C.c_double, C.c_double, _P, _P, _P]
+    L.orc_char_slope.restype = None
+    L.orc_char_slope.argtypes = [_P, _P, _P, C.c_double, C.c_double, _P]
+    L.orc_switch_logits.restype = None
+    L.orc_switch_logits.argtypes = [C.POINTER(_Cfg), PP, PF, _P]
+    return L
 
 
 def _ptr(a: np.ndarray):

@@ -48,6 +48,11 @@ class mhd_stats(C.Structure):
                 ("last_dt", C.c_double), ("status", C.c_int), ("steps", C.c_int)]
 
 
+class mhd_pipe_peaks(C.Structure):
+    _fields_ = [("fp64_fma_tflops", C.c_double), ("fp32_fma_tflops", C.c_double),
+                ("bf16_mma_sync_tflops", C.c_double), ("ms", C.c_double * 3)]
+
+
 class MHDError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"[{code}] {msg}")
@@ -64,7 +69,7 @@ EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state",
            "mhd_batch_set_barrier_timeout", "mhd_batch_inject_missed_arrival", "mhd_batch_box_dt",
            "mhd_batch_get_stats", "mhd_batch_destroy", "mhd_batch_last_error",
            "mlp_param_bytes", "mlp_init", "mlp_forward", "mlp_backward", "mlp_adam", "mhd_dump_faces",
-           "mhd_set_switch", "mhd_switch_choices"]
+           "mhd_set_switch", "mhd_switch_choices", "mhd_measure_pipe_peaks"]
 
 _lib = None
 
@@ -154,6 +159,8 @@ def load(build: bool = True):
     L.mhd_set_switch.argtypes = [_H, _VP, C.c_double]
     L.mhd_switch_choices.restype = C.c_int
     L.mhd_switch_choices.argtypes = [_H, _VP, _VP]
+    L.mhd_measure_pipe_peaks.restype = C.c_int
+    L.mhd_measure_pipe_peaks.argtypes = [_VP, C.POINTER(mhd_pipe_peaks)]
     L.mhd_last_error.restype = C.c_char_p
     L.mhd_last_error.argtypes = [_H]
     _lib = L
@@ -224,6 +231,14 @@ def mhd_divb_max(h) -> float:
     out = C.c_double()
     _check(h, load().mhd_divb_max(h, C.byref(out)))
     return out.value
+
+
+def mhd_measure_pipe_peaks(stream=None) -> dict:
+    """Measured FP64-FMA, FP32-FMA and BF16 mma.sync peaks (TFLOP/s) of the current device."""
+    p = mhd_pipe_peaks()
+    _check(None, load().mhd_measure_pipe_peaks(_VP(stream or 0), C.byref(p)))
+    return {"fp64_fma_tflops": p.fp64_fma_tflops, "fp32_fma_tflops": p.fp32_fma_tflops,
+            "bf16_mma_sync_tflops": p.bf16_mma_sync_tflops, "ms": list(p.ms)}
 
 
 def mhd_get_stats(h) -> dict:
