@@ -138,6 +138,31 @@ int mhd_get_state(mhd_handle* h, void* cell[5], void* face[3], int on_device);
  * the status word. */
 int mhd_step(mhd_handle* h, double dt, int nsteps);
 
+/* ---- host streaming -------------------------------------------------------
+ * Advance a sequence of independent states held in host memory by one step
+ * each (an ensemble, or a server of states): mhd_stream_step enqueues the copy
+ * of (cell_in, face_in) to the device on the handle's input copy stream, one
+ * step of it (dt as in mhd_step: dt <= 0 takes the CFL dt of that input) on
+ * the handle's stream, and the copy of the result to (cell_out, face_out) on
+ * its output copy stream, and returns.  Consecutive calls alternate between
+ * two input and two output device slots, so the copies of one state overlap
+ * the step of the next: with pinned host buffers a stream of states runs at
+ * the rate of the slowest of the three (host-to-device, step,
+ * device-to-host) instead of their sum.  Arrays are laid out as in
+ * mhd_set_state, element type as the state (FP32 in MHD_FP32, else FP64).
+ * Ownership: every host buffer passed since the last mhd_stream_sync must
+ * stay valid and unmodified, and outputs must not be read, until
+ * mhd_stream_sync returns; no other call may use the handle in between.  The
+ * first call allocates two extra device states.  After mhd_stream_sync the
+ * handle's current state is the last result.  Errors: MHD_ERR_INVALID (null
+ * pointers, NaN dt, learned switch without a network), MHD_ERR_NOMEM,
+ * MHD_ERR_CUDA; mhd_stream_sync also returns MHD_ERR_NONFINITE when a step met
+ * a non-finite value. */
+int mhd_stream_step(mhd_handle* h, const void* const cell_in[5], const void* const face_in[3], void* cell_out[5],
+                    void* face_out[3], double dt);
+/* Wait until every streamed step and its copies have completed. */
+int mhd_stream_sync(mhd_handle* h);
+
 /* Enqueue nsteps steps like mhd_step (dt <= 0: device-side CFL dt) without
  * synchronising and without checking the status word (timing loops, CUDA-graph
  * capture); the next synchronising call reports any device condition. */

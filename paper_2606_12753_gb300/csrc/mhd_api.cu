@@ -168,6 +168,15 @@ struct mhd_handle {
   std::vector<cudaEvent_t> ev_pool;        // 3 events per recorded step
   size_t ev_used = 0;
   std::string err;
+  // host streaming (mhd_stream_step): the state buffers the handle owns (the
+  // U pointers rotate over them), the two input slots, the copy streams and
+  // the events that order slot reuse between the three streams
+  std::vector<void*> owned_states;
+  void* slot_in[2] = {nullptr, nullptr};
+  void* slot_out[2] = {nullptr, nullptr};
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
+  long long nstream = 0;                   // streamed steps since the handle was created
 };
 
 static std::string g_create_err;
@@ -320,6 +329,7 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   const size_t wbytes = (size_t)h->geo.ncell * NW * h->welem;
   if (e == cudaSuccess) e = cudaMalloc(&h->U[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->U[1], bytes);
+  h->owned_states = {h->U[0], h->U[1]};
   if (e == cudaSuccess) e = cudaMalloc(&h->K1, kbytes);
   if (e == cudaSuccess && cfg->integrator == MHD_RK3) e = cudaMalloc(&h->Urk[0], bytes);
   if (e == cudaSuccess && cfg->integrator == MHD_RK3) e = cudaMalloc(&h->Urk[1], bytes);
@@ -359,8 +369,16 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
 extern "C" void mhd_destroy(mhd_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
-  cudaFree(h->U[0]);
-  cudaFree(h->U[1]);
+  if (h->s_in) cudaStreamSynchronize(h->s_in);
+  if (h->s_out) cudaStreamSynchronize(h->s_out);
+  for (void* p : h->owned_states) cudaFree(p);
+  for (int p = 0; p < 2; ++p) {
+    if (h->ev_h2d[p]) cudaEventDestroy(h->ev_h2d[p]);
+    if (h->ev_comp[p]) cudaEventDestroy(h->ev_comp[p]);
+    if (h->ev_d2h[p]) cudaEventDestroy(h->ev_d2h[p]);
+  }
+  if (h->s_in) cudaStreamDestroy(h->s_in);
+  if (h->s_out) cudaStreamDestroy(h->s_out);
   cudaFree(h->K1);
   cudaFree(h->Urk[0]);
   cudaFree(h->Urk[1]);
@@ -548,6 +566,91 @@ static int check_status(mhd_handle* h) {
   if (st & ST_NONFINITE) return fail(h, MHD_ERR_NONFINITE, "non-finite state value met on the device");
   if (st & ST_TIMEOUT) return fail(h, MHD_ERR_TIMEOUT, "device barrier timed out");
   return MHD_OK;
+}
+
+// ---- host streaming ---------------------------------------------------------
+
+static int stream_setup(mhd_handle* h) {
+  if (h->s_in) return MHD_OK;
+  const size_t bytes = (size_t)h->geo.total * h->elem;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    e = cudaMalloc(&h->slot_in[p], bytes);
+    if (e == cudaSuccess) h->owned_states.push_back(h->slot_in[p]);
+  }
+  // the output slots are the handle's own state buffers
+  h->slot_out[0] = h->owned_states[0];
+  h->slot_out[1] = h->owned_states[1];
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    e = cudaEventCreateWithFlags(&h->ev_h2d[p], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[p], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_d2h[p], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? MHD_ERR_NOMEM : MHD_ERR_CUDA;
+    cudaGetLastError();
+    return fail(h, code, "streaming setup failed: %s", cudaGetErrorString(e));
+  }
+  return MHD_OK;
+}
+
+static cudaError_t copy_state_async(const mhd_handle* h, bool in, char* dev, void* const* cell, void* const* face,
+                                    cudaStream_t st) {
+  const cudaMemcpyKind kind = in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < 5 && e == cudaSuccess; ++v) {
+    char* d = dev + (size_t)v * h->geo.ncell * h->elem;
+    const size_t n = (size_t)h->geo.ncell * h->elem;
+    e = in ? cudaMemcpyAsync(d, cell[v], n, kind, st) : cudaMemcpyAsync(cell[v], d, n, kind, st);
+  }
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    char* d = dev + (size_t)h->geo.face_off[k] * h->elem;
+    const size_t n = (size_t)face_count(h->geo, k) * h->elem;
+    e = in ? cudaMemcpyAsync(d, face[k], n, kind, st) : cudaMemcpyAsync(face[k], d, n, kind, st);
+  }
+  return e;
+}
+
+extern "C" int mhd_stream_step(mhd_handle* h, const void* const cell_in[5], const void* const face_in[3],
+                               void* cell_out[5], void* face_out[3], double dt) {
+  if (!h) return MHD_ERR_INVALID;
+  if (!cell_in || !face_in || !cell_out || !face_out) return fail(h, MHD_ERR_INVALID, "null state pointer array");
+  for (int v = 0; v < 5; ++v)
+    if (!cell_in[v] || !cell_out[v]) return fail(h, MHD_ERR_INVALID, "null cell array %d", v);
+  for (int k = 0; k < 3; ++k)
+    if (!face_in[k] || !face_out[k]) return fail(h, MHD_ERR_INVALID, "null face array %d", k);
+  if (dt != dt) return fail(h, MHD_ERR_INVALID, "dt is NaN");
+  if (int rc = need_switch(h)) return rc;
+  if (int rc = stream_setup(h)) return rc;
+  const int p = (int)(h->nstream & 1);
+  // input: slot p is free once the step that read it (two back) has run
+  CUDA_TRY(h, cudaStreamWaitEvent(h->s_in, h->ev_comp[p], 0));
+  CUDA_TRY(h, copy_state_async(h, true, (char*)h->slot_in[p], (void* const*)cell_in, (void* const*)face_in, h->s_in));
+  CUDA_TRY(h, cudaEventRecord(h->ev_h2d[p], h->s_in));
+  // compute: after the input arrived and the output slot's previous copy-out
+  CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_h2d[p], 0));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_d2h[p], 0));
+  h->U[h->cur] = h->slot_in[p];
+  h->U[h->cur ^ 1] = h->slot_out[p];
+  h->prims_valid = false;
+  if (int rc = enqueue_steps(h, dt, 1)) return rc;
+  if (dt > 0.0) h->last_dt = dt;
+  CUDA_TRY(h, cudaEventRecord(h->ev_comp[p], h->stream));
+  // output: the new state, now U[cur] = slot_out[p]
+  CUDA_TRY(h, cudaStreamWaitEvent(h->s_out, h->ev_comp[p], 0));
+  CUDA_TRY(h, copy_state_async(h, false, (char*)h->U[h->cur], cell_out, face_out, h->s_out));
+  CUDA_TRY(h, cudaEventRecord(h->ev_d2h[p], h->s_out));
+  h->nstream++;
+  return MHD_OK;
+}
+
+extern "C" int mhd_stream_sync(mhd_handle* h) {
+  if (!h) return MHD_ERR_INVALID;
+  if (h->s_in) CUDA_TRY(h, cudaStreamSynchronize(h->s_in));
+  if (h->s_out) CUDA_TRY(h, cudaStreamSynchronize(h->s_out));
+  return check_status(h);
 }
 
 extern "C" int mhd_step_async(mhd_handle* h, double dt, int nsteps) {

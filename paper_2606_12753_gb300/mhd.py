@@ -69,7 +69,8 @@ EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state",
            "mhd_batch_set_barrier_timeout", "mhd_batch_inject_missed_arrival", "mhd_batch_box_dt",
            "mhd_batch_get_stats", "mhd_batch_destroy", "mhd_batch_last_error",
            "mlp_param_bytes", "mlp_init", "mlp_forward", "mlp_backward", "mlp_adam", "mhd_dump_faces",
-           "mhd_set_switch", "mhd_switch_choices", "mhd_measure_pipe_peaks"]
+           "mhd_set_switch", "mhd_switch_choices", "mhd_measure_pipe_peaks", "mhd_stream_step",
+           "mhd_stream_sync"]
 
 _lib = None
 
@@ -159,6 +160,10 @@ def load(build: bool = True):
     L.mhd_set_switch.argtypes = [_H, _VP, C.c_double]
     L.mhd_switch_choices.restype = C.c_int
     L.mhd_switch_choices.argtypes = [_H, _VP, _VP]
+    L.mhd_stream_step.restype = C.c_int
+    L.mhd_stream_step.argtypes = [_H, _VP * 5, _VP * 3, _VP * 5, _VP * 3, C.c_double]
+    L.mhd_stream_sync.restype = C.c_int
+    L.mhd_stream_sync.argtypes = [_H]
     L.mhd_measure_pipe_peaks.restype = C.c_int
     L.mhd_measure_pipe_peaks.argtypes = [_VP, C.POINTER(mhd_pipe_peaks)]
     L.mhd_last_error.restype = C.c_char_p
@@ -231,6 +236,16 @@ def mhd_divb_max(h) -> float:
     out = C.c_double()
     _check(h, load().mhd_divb_max(h, C.byref(out)))
     return out.value
+
+
+def mhd_stream_step(h, cell_in, face_in, cell_out, face_out, dt: float):
+    """Enqueue copy-in, one step and copy-out of one host state (pointers)."""
+    _check(h, load().mhd_stream_step(h, (_VP * 5)(*cell_in), (_VP * 3)(*face_in), (_VP * 5)(*cell_out),
+                                     (_VP * 3)(*face_out), dt))
+
+
+def mhd_stream_sync(h):
+    _check(h, load().mhd_stream_sync(h))
 
 
 def mhd_measure_pipe_peaks(stream=None) -> dict:
@@ -336,6 +351,18 @@ class Solver:
 
     def step_async(self, dt: float, nsteps: int = 1):
         mhd_step_async(self.h, dt, nsteps)
+
+    def stream_step(self, cell_in, face_in, cell_out, face_out, dt: float = -1.0):
+        """Enqueue one streamed step of a host state: arrays with ``data_ptr``
+        (pinned torch CPU tensors) or numpy arrays of the handle's element
+        type, which must stay alive and untouched until stream_sync()."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        mhd_stream_step(self.h, [ptr(cell_in[v]) for v in range(5)], [ptr(f) for f in face_in],
+                        [ptr(cell_out[v]) for v in range(5)], [ptr(f) for f in face_out], dt)
+
+    def stream_sync(self):
+        mhd_stream_sync(self.h)
 
     def cfl_dt(self) -> float:
         return mhd_cfl_dt(self.h)
