@@ -48,13 +48,12 @@ struct Tile {
   static constexpr int oEZ = oEXY + 2 * 2 * nE;
   static constexpr int oDU = oEZ + nE;
   static constexpr int nRtot = oDU + 2 * 5 * nC;
-  // new face values (type S): NBX[nE], NBY[nE], NBZ[2][nC] (z-faces by parity)
-  static constexpr int nS = 2 * nE + 2 * nC;
+  // flux items of one plane: z-faces, x-faces, y-faces; the learned switch
+  // queues their indices (unsigned short) in a region of its own
+  static constexpr int nItems = nZ + nX + nY;
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
   static constexpr int nI = W + H + 6;   // column/row maps, switch counters, the stage's dt
-  // flux items of one plane: z-faces, x-faces, y-faces
-  static constexpr int nItems = nZ + nX + nY;
   // per-cell slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
   // x and y slopes of the current plane, z slopes of two planes (by parity)
   static constexpr int nSl = 7 * nZ;
@@ -63,7 +62,7 @@ struct Tile {
   __host__ __device__ static constexpr size_t core_bytes() {
     size_t b = (size_t)nRtot * sizeof(R);
     b = (b + 15) / 16 * 16;
-    b += (size_t)nS * sizeof(S);
+    b += (size_t)nItems * sizeof(unsigned short);
     b = (b + 15) / 16 * 16;
     b += (size_t)nI * sizeof(int);
     return (b + 15) / 16 * 16;
@@ -704,78 +703,55 @@ struct StageKernel {
   }
 
   // ---------------------------------------------------------------- phase D
-  static __device__ __forceinline__ void new_faces(const Geo& g, const StageArgs& a, R* sm, S* NB, const StepDt& dt,
-                                                   int gi0, int gj0, int k, int kb, int ke) {
-    const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]), idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
+  // Phase D in one pass: each cell of plane k advances its six faces from
+  // the edge EMFs (-curl E; a face shared by two cells is advanced by both,
+  // with identical arithmetic) and its five conserved values, stores the
+  // faces it owns (its lower faces, and the top face of an outflow axis),
+  // then recovers its primitives from its own new faces.  No face values pass
+  // through shared memory, so no barrier separates faces from cells.
+  static __device__ __forceinline__ void update_plane(const Geo& g, const StageArgs& a, R* sm, const StepDt& dt,
+                                                      int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
+                                                      bool& bad, R& smax) {
+    const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]),
+            idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
     const R* EZ = sm + T::oEZ;
-    const R* EX0 = sm + T::oEXY + (k & 1) * 2 * T::nE;   // k-1/2
+    const R* EX0 = sm + T::oEXY + (k & 1) * 2 * T::nE;         // k-1/2
     const R* EY0 = EX0 + T::nE;
     const R* EX1 = sm + T::oEXY + ((k + 1) & 1) * 2 * T::nE;   // k+1/2
     const R* EY1 = EX1 + T::nE;
-    S* NBX = NB;
-    S* NBY = NB + T::nE;
-    S* NBZ = NB + 2 * T::nE;
+    const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
+    R* Wout = (R*)a.Wout;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const bool outx = g.bc[0] == 1, outy = g.bc[1] == 1, outz = g.bc[2] == 1;
-    for (int e = threadIdx.x; e < T::nE; e += blockDim.x) {
-      const int i = e % (TX + 1), j = e / (TX + 1);
-      const int gi = gi0 + i, gj = gj0 + j;
-      // B_x on face (i-1/2, j, k): needed for i in [0, TX] within the domain
-      if (j < TY && gj < ny && gi <= nx) {
-        const int fi = gi == nx && !outx ? 0 : gi;
-        const long long f = xface_index(g, fi, gj, k);
-        const R l = -((EZ[e + (TX + 1)] - EZ[e]) * idy - (EY1[e] - EY0[e]) * idz);
-        const S v = advance(a, f, l, dt);
-        NBX[e] = v;
-        if ((i < TX && gi < nx) || (outx && gi == nx)) emit(a, f, l, v);
-      }
-      // B_y on face (i, j-1/2, k)
-      if (i < TX && gi < nx && gj <= ny) {
-        const int fj = gj == ny && !outy ? 0 : gj;
-        const long long f = yface_index(g, gi, fj, k);
-        const R l = -((EX1[e] - EX0[e]) * idz - (EZ[e + 1] - EZ[e]) * idx);
-        const S v = advance(a, f, l, dt);
-        NBY[e] = v;
-        if ((j < TY && gj < ny) || (outy && gj == ny)) emit(a, f, l, v);
-      }
-      // B_z on the faces k-1/2 and k+1/2 of cell (i, j), kept by face parity
-      // (slot m & 1 holds face m): face k+1/2 computed here is face k-1/2 of
-      // the next plane, so only the first plane of a chunk computes its lower
-      // face.  A face is emitted by the plane whose lower face it is, and the
-      // top face of an outflow axis by the last plane.
-      if (i < TX && j < TY && gi < nx && gj < ny) {
-        const int c = i + TX * j;
-        if (k == kb) {
-          const long long flo = zface_index(g, gi, gj, k);
-          const R llo = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
-          const S vlo = advance(a, flo, llo, dt);
-          NBZ[(k & 1) * T::nC + c] = vlo;
-          emit(a, flo, llo, vlo);
-        }
-        const int khi = k + 1 == nz && !outz ? 0 : k + 1;
-        const long long fhi = zface_index(g, gi, gj, khi);
-        const R lhi = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
-        const S vhi = advance(a, fhi, lhi, dt);
-        NBZ[((k + 1) & 1) * T::nC + c] = vhi;
-        if (k + 1 < ke || (outz && k + 1 == nz)) emit(a, fhi, lhi, vhi);
-      }
-    }
-  }
-
-  static __device__ __forceinline__ void new_cells(const Geo& g, const StageArgs& a, R* sm, const S* NB,
-                                                   const StepDt& dt,
-                                                   int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
-                                                   bool& bad, R& smax) {
-    const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
-    const S* NBX = NB;
-    const S* NBY = NB + T::nE;
-    const S* NBZ = NB + 2 * T::nE;
-    R* Wout = (R*)a.Wout;
-    const int nx = g.n[0], ny = g.n[1];
     for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
       const int i = c % TX, j = c / TX;
       const int gi = gi0 + i, gj = gj0 + j;
       if (gi >= nx || gj >= ny) continue;
+      const int e = i + (TX + 1) * j;            // edge/face slot of the cell's lower corner
+      // increments of the six faces
+      const R lx0 = -((EZ[e + (TX + 1)] - EZ[e]) * idy - (EY1[e] - EY0[e]) * idz);
+      const R lx1 = -((EZ[e + 1 + (TX + 1)] - EZ[e + 1]) * idy - (EY1[e + 1] - EY0[e + 1]) * idz);
+      const R ly0 = -((EX1[e] - EX0[e]) * idz - (EZ[e + 1] - EZ[e]) * idx);
+      const R ly1 = -((EX1[e + (TX + 1)] - EX0[e + (TX + 1)]) * idz -
+                      (EZ[e + 1 + (TX + 1)] - EZ[e + (TX + 1)]) * idx);
+      const R lz0 = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
+      const R lz1 = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
+      // their global indices (periodic axes wrap the top face to 0)
+      const long long fx0 = xface_index(g, gi, gj, k);
+      const long long fx1 = xface_index(g, gi + 1 == nx && !outx ? 0 : gi + 1, gj, k);
+      const long long fy0 = yface_index(g, gi, gj, k);
+      const long long fy1 = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
+      const long long fz0 = zface_index(g, gi, gj, k);
+      const long long fz1 = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
+      const S bx0 = advance(a, fx0, lx0, dt), bx1 = advance(a, fx1, lx1, dt);
+      const S by0 = advance(a, fy0, ly0, dt), by1 = advance(a, fy1, ly1, dt);
+      const S bz0 = advance(a, fz0, lz0, dt), bz1 = advance(a, fz1, lz1, dt);
+      emit(a, fx0, lx0, bx0);
+      emit(a, fy0, ly0, by0);
+      emit(a, fz0, lz0, bz0);
+      if (outx && gi + 1 == nx) emit(a, fx1, lx1, bx1);
+      if (outy && gj + 1 == ny) emit(a, fy1, ly1, by1);
+      if (outz && k + 1 == nz) emit(a, fz1, lz1, bz1);
       const long long s = (long long)gi + (long long)nx * ((long long)gj + (long long)ny * k);
       double u[5];
 #pragma unroll
@@ -786,12 +762,10 @@ struct StageKernel {
         u[v] = (double)nv;
       }
       if (!a.Wout) continue;   // operator evaluation only (mhd_rhs)
-      const int e = i + (TX + 1) * j;
       R w[NW];
       int hr, hp;
-      recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], (double)NBX[e], (double)NBX[e + 1], (double)NBY[e],
-                    (double)NBY[e + (TX + 1)], (double)NBZ[(k & 1) * T::nC + c],
-                    (double)NBZ[((k + 1) & 1) * T::nC + c], w, hr, hp);
+      recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], (double)bx0, (double)bx1, (double)by0, (double)by1,
+                    (double)bz0, (double)bz1, w, hr, hp);
       nrho += hr;
       np += hp;
       if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
@@ -835,17 +809,12 @@ struct StageKernel {
   // CTA calls this with the same arguments.
   static __device__ void run_item(const Geo& g, const StageArgs& a, int item, unsigned char* smem_raw) {
     R* sm = reinterpret_cast<R*>(smem_raw);
-    constexpr size_t sOff = ((size_t)T::nRtot * sizeof(R) + 15) / 16 * 16;
-    S* NB = reinterpret_cast<S*>(smem_raw + sOff);
-    constexpr size_t iOff = ((sOff + (size_t)T::nS * sizeof(S)) + 15) / 16 * 16;
+    constexpr size_t qOff = ((size_t)T::nRtot * sizeof(R) + 15) / 16 * 16;
+    unsigned short* queue = reinterpret_cast<unsigned short*>(smem_raw + qOff);   // learned switch only
+    constexpr size_t iOff = ((qOff + (size_t)T::nItems * sizeof(unsigned short)) + 15) / 16 * 16;
     int* colc = reinterpret_cast<int*>(smem_raw + iOff);
     int* rowc = colc + W;
     int* qcnt = rowc + T::H;
-    // the HLLD queue of the learned switch lives in the x- and y-face part of
-    // the new-face buffer, which is idle from the start of the flux phase to
-    // new_faces (the z-face part carries face k+1/2 over to the next plane)
-    unsigned short* queue = reinterpret_cast<unsigned short*>(NB);
-    static_assert((size_t)T::nItems * sizeof(unsigned short) <= (size_t)2 * T::nE * sizeof(S), "queue does not fit");
     constexpr size_t sl_off = T::template core_bytes<R, S>();
     R* sl = reinterpret_cast<R*>(smem_raw + sl_off);   // used when SLOPES
 
@@ -905,9 +874,7 @@ struct StageKernel {
       __syncthreads();
       edges_2d(g, sm);
       __syncthreads();
-      new_faces(g, a, sm, NB, sdt, gi0, gj0, 0, 0, 1);
-      __syncthreads();
-      new_cells(g, a, sm, NB, sdt, gi0, gj0, 0, nrho, np, bad, smax);
+      update_plane(g, a, sm, sdt, gi0, gj0, 0, nrho, np, bad, smax);
       finish(a, nrho, np, nh, nd, bad, smax);
       return;
     }
@@ -940,11 +907,7 @@ struct StageKernel {
       __syncthreads();
       divergence_and_edges(g, sm, k);
       __syncthreads();
-      if (k >= kb) {
-        new_faces(g, a, sm, NB, sdt, gi0, gj0, k, kb, ke);
-        __syncthreads();
-        new_cells(g, a, sm, NB, sdt, gi0, gj0, k, nrho, np, bad, smax);
-      }
+      if (k >= kb) update_plane(g, a, sm, sdt, gi0, gj0, k, nrho, np, bad, smax);
     }
 
     finish(a, nrho, np, nh, nd, bad, smax);
