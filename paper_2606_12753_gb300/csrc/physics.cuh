@@ -28,7 +28,60 @@ template <> struct Eps<float> { static constexpr float degen = 1e-6f; };
 template <typename R> __host__ __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 template <typename R> __host__ __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 template <typename R> __host__ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
-__host__ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+
+// Reciprocal, square root and reciprocal square root.  FP32: the hardware
+// instructions (the FP32-bulk units are compiled with approximate divide and
+// square root).  FP64 on the device: the PTX approximate seeds
+// rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64 (measured relative error ~1e-6)
+// refined by one third-order step, which cubes that error (~1e-18, so the
+// result is within a few ulp of the IEEE one), in three to five FP64-pipe
+// operations instead of an IEEE-rounded sequence (GB300 issues one FP64
+// warp-instruction per ~17 SM cycles).  The steps are the truncated series
+//   1/x        = r0 / (1 - e)       ~ r0 (1 + e + e^2),          e = 1 - x r0
+//   1/sqrt(x)  = y0 (1 - h)^(-1/2)  ~ y0 (1 + h/2 + 3 h^2/8),    h = 1 - x y0^2
+// and sqrt(x) = x / sqrt(x).  Zero, subnormal, infinite, NaN and (for the
+// roots) negative inputs, recognised with integer tests, take the IEEE
+// operation.
+__host__ __device__ __forceinline__ bool f64_plain(double x) {
+#ifdef __CUDA_ARCH__
+  const int e = __double2hiint(x) & 0x7ff00000;
+  return e != 0 && e != 0x7ff00000;
+#else
+  return false;
+#endif
+}
+__host__ __device__ __forceinline__ double rcp_(double x) {
+#ifdef __CUDA_ARCH__
+  if (!f64_plain(x)) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+#else
+  return 1.0 / x;
+#endif
+}
+__host__ __device__ __forceinline__ double rrsqrt_(double x) {
+#ifdef __CUDA_ARCH__
+  if (!f64_plain(x) || __double2hiint(x) < 0) return 1.0 / sqrt(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = fma(-(x * y), y, 1.0);
+  return fma(y, h * fma(0.375, h, 0.5), y);
+#else
+  return 1.0 / sqrt(x);
+#endif
+}
+__host__ __device__ __forceinline__ double rsqrt_(double x) {   // square root
+#ifdef __CUDA_ARCH__
+  if (!f64_plain(x) || __double2hiint(x) < 0) return sqrt(x);
+  return x * rrsqrt_(x);
+#else
+  return sqrt(x);
+#endif
+}
+__host__ __device__ __forceinline__ float rcp_(float x) { return 1.0f / x; }
+__host__ __device__ __forceinline__ float rrsqrt_(float x) { return rsqrtf(x); }
 __host__ __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 
 // Sign-bit helpers (integer operations: they keep the sign tests of the
@@ -80,13 +133,13 @@ __host__ __device__ __forceinline__ R fast_speed_r(const R* w, R bn, R gamma, R 
 
 template <typename R>
 __host__ __device__ __forceinline__ R fast_speed(const R* w, R bn, R gamma) {
-  return fast_speed_r(w, bn, gamma, R(1) / w[0]);
+  return fast_speed_r(w, bn, gamma, rcp_(w[0]));
 }
 
 // Fast speeds of both states of a face from one reciprocal of rho_L rho_R.
 template <typename R>
 __host__ __device__ __forceinline__ void fast_speeds(const R* wl, const R* wr, R bn, R gamma, R& cl, R& cr) {
-  const R r = R(1) / (wl[0] * wr[0]);
+  const R r = rcp_(wl[0] * wr[0]);
   cl = fast_speed_r(wl, bn, gamma, wr[0] * r);
   cr = fast_speed_r(wr, bn, gamma, wl[0] * r);
 }
@@ -138,7 +191,7 @@ __host__ __device__ __forceinline__ void hll_flux_g(const R* wl, const R* wr, R 
   phys_flux_i(wr, bn, ig, fr);
   R ul[7] = {wl[0], wl[0] * wl[1], wl[0] * wl[2], wl[0] * wl[3], total_energy_i(wl, bn, ig), wl[5], wl[6]};
   R ur[7] = {wr[0], wr[0] * wr[1], wr[0] * wr[2], wr[0] * wr[3], total_energy_i(wr, bn, ig), wr[5], wr[6]};
-  R inv = R(1) / (sr - sl);
+  R inv = rcp_(sr - sl);
 #pragma unroll
   for (int q = 0; q < 7; ++q) f[q] = (sr * fl[q] - sl * fr[q] + sl * sr * (ur[q] - ul[q])) * inv;
 }
@@ -154,12 +207,6 @@ struct Star {
   R rho, v, w, by, bz, e, vb, sq, isq;   // sq = sqrt(rho*), isq = 1/sqrt(rho*)
 };
 
-template <typename R>
-__host__ __device__ __forceinline__ R rrsqrt_(R x);
-template <>
-__host__ __device__ __forceinline__ double rrsqrt_<double>(double x) { return rsqrt(x); }
-template <>
-__host__ __device__ __forceinline__ float rrsqrt_<float>(float x) { return rsqrtf(x); }
 
 template <typename R>
 __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, R s, R sm, R pts) {
@@ -173,11 +220,11 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
   R scale = rmax(rabs(num), bn2);
   R inv_ssm;
   if (rabs(den) <= Eps<R>::degen * scale) {
-    inv_ssm = R(1) / ssm;
+    inv_ssm = rcp_(ssm);
     st.v = v; st.w = ww; st.by = by; st.bz = bz;
   } else {
     // 1/(S - S_M) and 1/den from one reciprocal of their product
-    const R r = R(1) / (ssm * den);
+    const R r = rcp_(ssm * den);
     inv_ssm = den * r;
     R iden = ssm * r;
     R c1 = bn * (sm - u) * iden;
@@ -193,7 +240,7 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
   R pt = w[4] + R(0.5) * (bn2 + by * by + bz * bz);
   R e = total_energy_i(w, bn, igm1);
   st.e = (sd * e - pt * u + pts * sm + bn * (vb - st.vb)) * inv_ssm;
-  st.isq = rrsqrt_<R>(st.rho);
+  st.isq = rrsqrt_(st.rho);
   st.sq = st.rho * st.isq;
   return st;
 }
@@ -215,7 +262,7 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
   R ptl = wl[4] + R(0.5) * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6]);
   R ptr = wr[4] + R(0.5) * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6]);
   R sdl = sl - wl[1], sdr = sr - wr[1];
-  R sm = (sdr * wr[0] * wr[1] - sdl * wl[0] * wl[1] - ptr + ptl) / (sdr * wr[0] - sdl * wl[0]);
+  R sm = (sdr * wr[0] * wr[1] - sdl * wl[0] * wl[1] - ptr + ptl) * rcp_(sdr * wr[0] - sdl * wl[0]);
   R pts = ptl + wl[0] * sdl * (sm - wl[1]);
   Star<R> L = star_side(wl, bn, ig, sl, sm, pts);
   Star<R> Rr = star_side(wr, bn, ig, sr, sm, pts);
@@ -235,7 +282,7 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
   for (int q = 0; q < 7; ++q) f[q] = fo[q] + so * (us[q] - uo[q]);
   if (dbl) {
     R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
-    R isq = R(1) / (L.sq + Rr.sq);
+    R isq = rcp_(L.sq + Rr.sq);
     R vss = (L.sq * L.v + Rr.sq * Rr.v + (Rr.by - L.by) * sgn) * isq;
     R wss = (L.sq * L.w + Rr.sq * Rr.w + (Rr.bz - L.bz) * sgn) * isq;
     R byss = (L.sq * Rr.by + Rr.sq * L.by + L.sq * Rr.sq * (Rr.v - L.v) * sgn) * isq;
@@ -307,21 +354,24 @@ template <typename R>
 __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, const R* wp, R bn0, R gamma,
                                                     R* slope) {
   const R rho = w0[0];
-  const R ir = R(1) / rho;
-  const R a2 = gamma * w0[4] * ir, a = rsqrt_(a2), sr = rsqrt_(rho), isr = R(1) / sr;
+  const R ir = rcp_(rho);
+  const R a2 = gamma * w0[4] * ir, a = rsqrt_(a2), sr = rsqrt_(rho), isr = rcp_(sr);
   const R bnr = bn0 * isr, b1 = w0[5] * isr, b2 = w0[6] * isr;
   const R bt2 = b1 * b1 + b2 * b2, bsq = bnr * bnr + bt2;
   // forms without cancellation: c_f^2 - c_s^2 = sqrt((a^2-b^2)^2 + 4 a^2 b_t^2),
   // c_s^2 = a^2 b_n^2 / c_f^2, and below c_f^2 - a^2, a^2 - c_s^2 as half-sums
   // with that root (alpha_s is otherwise the root of a rounding residue when
   // B_t vanishes)
-  const R sq = rsqrt_((a2 - bsq) * (a2 - bsq) + R(4) * a2 * bt2);
+  // IEEE square root here: sqrt(fl(d*d)) = |d| exactly when B_t = 0, which
+  // makes c_f^2 - a^2 or a^2 - c_s^2 below exactly zero (a root with a few
+  // ulp of error would leave a residue whose square root is ~1e-8)
+  const R sq = sqrt((a2 - bsq) * (a2 - bsq) + R(4) * a2 * bt2);
   const R cf2 = R(0.5) * (a2 + bsq + sq);
-  const R cs2 = cf2 > R(0) ? a2 * bnr * bnr / cf2 : R(0);
+  const R cs2 = cf2 > R(0) ? a2 * bnr * bnr * rcp_(cf2) : R(0);
   const R cf = rsqrt_(cf2), cs = rsqrt_(cs2), bt = rsqrt_(bt2);
   R be1, be2;
   if (bt > Eps<R>::degen * rsqrt_(a2 + bsq)) {
-    const R ib = R(1) / bt;
+    const R ib = rcp_(bt);
     be1 = b1 * ib;
     be2 = b2 * ib;
   } else {
@@ -329,7 +379,7 @@ __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, co
   }
   R af, as;
   if (sq > Eps<R>::degen * cf2) {
-    const R id = R(1) / sq;
+    const R id = rcp_(sq);
     const R fa = R(0.5) * (bsq - a2 + sq), as2 = R(0.5) * (a2 - bsq + sq);   // c_f^2 - a^2, a^2 - c_s^2
     af = rsqrt_((as2 > R(0) ? as2 : R(0)) * id);
     as = rsqrt_((fa > R(0) ? fa : R(0)) * id);
@@ -338,7 +388,7 @@ __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, co
     as = R(0);
   }
   const R sg = bn0 >= R(0) ? R(1) : R(-1);
-  const R i2a2 = R(0.5) / a2, i2r = i2a2 * ir, i2sa = R(0.5) * isr / a, i2s = R(0.5) * isr;
+  const R i2a2 = R(0.5) * rcp_(a2), i2r = i2a2 * ir, i2sa = R(0.5) * isr * rcp_(a), i2s = R(0.5) * isr;
   R dc[7];   // limited wave amplitudes: f-, a-, s-, e, s+, a+, f+
   {
     R m[7], q[7];

@@ -168,7 +168,7 @@ __device__ __forceinline__ void recover(const Geo& g, double rho, double mx, dou
   const double mm = mx * mx + my * my + mz * mz;
   const double bb = sx * sx + sy * sy + sz * sz;
   if (PREC == P_FP64) {
-    const double rinv = 1.0 / rho;
+    const double rinv = rcp_(rho);
     double p = g.gm1 * (e - 0.5 * mm * rinv - 0.125 * bb);
     p_hit = p < g.p_floor;
     if (p_hit) p = g.p_floor;
