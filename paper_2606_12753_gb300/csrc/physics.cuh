@@ -25,9 +25,37 @@ template <typename R> struct Eps;
 template <> struct Eps<double> { static constexpr double degen = 1e-12; };
 template <> struct Eps<float> { static constexpr float degen = 1e-6f; };
 
+// Comparisons.  FP32: the FP32 compare instructions.  FP64 on the device:
+// integer comparisons of the IEEE bit patterns, which keep them off the FP64
+// pipe (one warp-instruction per ~17 SM cycles on GB300; the integer pipes
+// are nearly idle in the FP64 form).  For non-NaN x the signed 64-bit key
+// k(x) = b ^ ((b >> 63) & 0x7fff...f), b the bit pattern, orders as x does
+// (with -0 just below +0); tests against zero use the sign and the pattern
+// directly, so +-0 compare as IEEE does.  NaN inputs are not ordered as
+// IEEE orders them (min/max may drop a NaN, as fmin/fmax do).
 template <typename R> __host__ __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 template <typename R> __host__ __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 template <typename R> __host__ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+template <typename R> __host__ __device__ __forceinline__ bool gt0(R x) { return x > R(0); }
+template <typename R> __host__ __device__ __forceinline__ bool lt0(R x) { return x < R(0); }
+template <typename R> __host__ __device__ __forceinline__ bool lt_(R a, R b) { return a < b; }
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+template <> __device__ __forceinline__ double rabs<double>(double x) { return fabs(x); }
+template <> __device__ __forceinline__ double rmin<double>(double a, double b) { return okey(a) < okey(b) ? a : b; }
+template <> __device__ __forceinline__ double rmax<double>(double a, double b) { return okey(a) > okey(b) ? a : b; }
+template <> __device__ __forceinline__ bool gt0<double>(double x) { return __double_as_longlong(x) > 0; }
+template <> __device__ __forceinline__ bool lt0<double>(double x) {
+  return (unsigned long long)__double_as_longlong(x) > 0x8000000000000000ull;
+}
+template <> __device__ __forceinline__ bool lt_<double>(double a, double b) { return okey(a) < okey(b); }
+#endif
+template <typename R> __host__ __device__ __forceinline__ bool ge0(R x) { return !lt0(x); }
+template <typename R> __host__ __device__ __forceinline__ bool le0(R x) { return !gt0(x); }
+template <typename R> __host__ __device__ __forceinline__ bool le_(R a, R b) { return !lt_(b, a); }
 
 // Reciprocal, square root and reciprocal square root.  FP32: the hardware
 // instructions (the FP32-bulk units are compiled with approximate divide and
@@ -102,7 +130,13 @@ __host__ __device__ __forceinline__ bool opposite_signs(float a, float b) {
 }
 __host__ __device__ __forceinline__ double copysign_(double m, double s) { return copysign(m, s); }
 __host__ __device__ __forceinline__ float copysign_(float m, float s) { return copysignf(m, s); }
-__host__ __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
+__host__ __device__ __forceinline__ double fmin_(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return rmin(a, b);
+#else
+  return fmin(a, b);
+#endif
+}
 __host__ __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 
 // MC-limited slope of the middle of three values: with dm = q0 - qm and
@@ -127,7 +161,7 @@ __host__ __device__ __forceinline__ R fast_speed_r(const R* w, R bn, R gamma, R 
   R b2 = (bn * bn + w[5] * w[5] + w[6] * w[6]) * rinv;
   R s = a2 + b2;
   R disc = s * s - R(4) * a2 * bn * bn * rinv;
-  disc = disc > R(0) ? disc : R(0);
+  disc = gt0(disc) ? disc : R(0);
   return rsqrt_(R(0.5) * (s + rsqrt_(disc)));
 }
 
@@ -184,8 +218,8 @@ __host__ __device__ __forceinline__ void hll_flux_g(const R* wl, const R* wr, R 
   if (cmax) *cmax = cm;
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
-  if (sl >= R(0)) { phys_flux_i(wl, bn, ig, f); return; }
-  if (sr <= R(0)) { phys_flux_i(wr, bn, ig, f); return; }
+  if (ge0(sl)) { phys_flux_i(wl, bn, ig, f); return; }
+  if (le0(sr)) { phys_flux_i(wr, bn, ig, f); return; }
   R fl[7], fr[7];
   phys_flux_i(wl, bn, ig, fl);
   phys_flux_i(wr, bn, ig, fr);
@@ -219,7 +253,7 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
   R den = num - bn2;
   R scale = rmax(rabs(num), bn2);
   R inv_ssm;
-  if (rabs(den) <= Eps<R>::degen * scale) {
+  if (le_(rabs(den), Eps<R>::degen * scale)) {
     inv_ssm = rcp_(ssm);
     st.v = v; st.w = ww; st.by = by; st.bz = bz;
   } else {
@@ -257,8 +291,8 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
   if (cmax) *cmax = cm;
   R sl = rmin(wl[1], wr[1]) - cm;
   R sr = rmax(wl[1], wr[1]) + cm;
-  if (sl > R(0)) { phys_flux_i(wl, bn, ig, f); return; }
-  if (sr < R(0)) { phys_flux_i(wr, bn, ig, f); return; }
+  if (gt0(sl)) { phys_flux_i(wl, bn, ig, f); return; }
+  if (lt0(sr)) { phys_flux_i(wr, bn, ig, f); return; }
   R ptl = wl[4] + R(0.5) * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6]);
   R ptr = wr[4] + R(0.5) * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6]);
   R sdl = sl - wl[1], sdr = sr - wr[1];
@@ -269,11 +303,11 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
   R abn = rabs(bn);
   R ssl = sm - abn * L.isq;
   R ssr = sm + abn * Rr.isq;
-  const bool left = sm >= R(0);
+  const bool left = ge0(sm);
   const R* w = left ? wl : wr;
   const Star<R>& S = left ? L : Rr;
   R so = left ? sl : sr;
-  bool dbl = left ? (ssl < R(0)) : (ssr >= R(0));
+  bool dbl = left ? lt0(ssl) : ge0(ssr);
   R fo[7];
   phys_flux_i(w, bn, ig, fo);
   R uo[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], total_energy_i(w, bn, ig), w[5], w[6]};
@@ -281,7 +315,7 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
 #pragma unroll
   for (int q = 0; q < 7; ++q) f[q] = fo[q] + so * (us[q] - uo[q]);
   if (dbl) {
-    R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
+    R sgn = gt0(bn) ? R(1) : (lt0(bn) ? R(-1) : R(0));
     R isq = rcp_(L.sq + Rr.sq);
     R vss = (L.sq * L.v + Rr.sq * Rr.v + (Rr.by - L.by) * sgn) * isq;
     R wss = (L.sq * L.w + Rr.sq * Rr.w + (Rr.bz - L.bz) * sgn) * isq;
@@ -307,13 +341,13 @@ __host__ __device__ __forceinline__ void hlld_flux(const R* wl, const R* wr, R b
 // instead of an arbitrary side.
 template <typename R>
 __host__ __device__ __forceinline__ R oriented_mass_flux(R f0, R rho_l, R rho_r, R cmax, R eps) {
-  return rabs(f0) <= eps * R(0.5) * (rho_l + rho_r) * cmax ? R(0) : f0;
+  return le_(rabs(f0), eps * R(0.5) * (rho_l + rho_r) * cmax) ? R(0) : f0;
 }
 
 // Gardiner-Stone upwind selection by the sign of a face mass flux.
 template <typename R>
 __host__ __device__ __forceinline__ R upwind(R m, R lo, R hi) {
-  return m > R(0) ? lo : (m < R(0) ? hi : R(0.5) * (lo + hi));
+  return gt0(m) ? lo : (lt0(m) ? hi : R(0.5) * (lo + hi));
 }
 
 // Edge EMF along c at the corner of the (a, b) plane (c, a, b cyclic), from
@@ -367,10 +401,10 @@ __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, co
   // ulp of error would leave a residue whose square root is ~1e-8)
   const R sq = sqrt((a2 - bsq) * (a2 - bsq) + R(4) * a2 * bt2);
   const R cf2 = R(0.5) * (a2 + bsq + sq);
-  const R cs2 = cf2 > R(0) ? a2 * bnr * bnr * rcp_(cf2) : R(0);
+  const R cs2 = gt0(cf2) ? a2 * bnr * bnr * rcp_(cf2) : R(0);
   const R cf = rsqrt_(cf2), cs = rsqrt_(cs2), bt = rsqrt_(bt2);
   R be1, be2;
-  if (bt > Eps<R>::degen * rsqrt_(a2 + bsq)) {
+  if (lt_(Eps<R>::degen * rsqrt_(a2 + bsq), bt)) {
     const R ib = rcp_(bt);
     be1 = b1 * ib;
     be2 = b2 * ib;
@@ -378,16 +412,16 @@ __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, co
     be1 = be2 = R(0.70710678118654752440);
   }
   R af, as;
-  if (sq > Eps<R>::degen * cf2) {
+  if (lt_(Eps<R>::degen * cf2, sq)) {
     const R id = rcp_(sq);
     const R fa = R(0.5) * (bsq - a2 + sq), as2 = R(0.5) * (a2 - bsq + sq);   // c_f^2 - a^2, a^2 - c_s^2
-    af = rsqrt_((as2 > R(0) ? as2 : R(0)) * id);
-    as = rsqrt_((fa > R(0) ? fa : R(0)) * id);
+    af = rsqrt_((gt0(as2) ? as2 : R(0)) * id);
+    as = rsqrt_((gt0(fa) ? fa : R(0)) * id);
   } else {
     af = R(1);
     as = R(0);
   }
-  const R sg = bn0 >= R(0) ? R(1) : R(-1);
+  const R sg = ge0(bn0) ? R(1) : R(-1);
   const R i2a2 = R(0.5) * rcp_(a2), i2r = i2a2 * ir, i2sa = R(0.5) * isr * rcp_(a), i2s = R(0.5) * isr;
   R dc[7];   // limited wave amplitudes: f-, a-, s-, e, s+, a+, f+
   {

@@ -162,7 +162,7 @@ __device__ __forceinline__ void recover(const Geo& g, double rho, double mx, dou
                                         double bxl, double bxh, double byl, double byh, double bzl, double bzh,
                                         typename Prec<PREC>::R* w, int& rho_hit, int& p_hit) {
   using R = typename Prec<PREC>::R;
-  rho_hit = rho < g.rho_floor;
+  rho_hit = lt_(rho, g.rho_floor);
   if (rho_hit) rho = g.rho_floor;
   const double sx = bxl + bxh, sy = byl + byh, sz = bzl + bzh;
   const double mm = mx * mx + my * my + mz * mz;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void recover(const Geo& g, double rho, double mx, dou
   if (PREC == P_FP64) {
     const double rinv = rcp_(rho);
     double p = g.gm1 * (e - 0.5 * mm * rinv - 0.125 * bb);
-    p_hit = p < g.p_floor;
+    p_hit = lt_(p, g.p_floor);
     if (p_hit) p = g.p_floor;
     w[0] = (R)rho; w[1] = (R)(mx * rinv); w[2] = (R)(my * rinv); w[3] = (R)(mz * rinv); w[4] = (R)p;
     w[5] = (R)(0.5 * sx); w[6] = (R)(0.5 * sy); w[7] = (R)(0.5 * sz);
@@ -180,7 +180,7 @@ __device__ __forceinline__ void recover(const Geo& g, double rho, double mx, dou
     const double r0 = widen(rf);
     const double r1 = fma(r0, fma(-rho, r0, 1.0), r0);
     double p = g.gm1 * (e - 0.5 * mm * r1 - 0.125 * bb);
-    p_hit = p < g.p_floor;
+    p_hit = lt_(p, g.p_floor);
     if (p_hit) p = g.p_floor;
     w[0] = rho_f; w[1] = narrow(mx) * rf; w[2] = narrow(my) * rf; w[3] = narrow(mz) * rf; w[4] = narrow(p);
     w[5] = 0.5f * narrow(sx); w[6] = 0.5f * narrow(sy); w[7] = 0.5f * narrow(sz);

@@ -1,7 +1,7 @@
 // Accuracy of the stage kernels' arithmetic helpers against the hardware's
 // IEEE operations: the FP64 reciprocal, reciprocal square root and square
-// root (approximate seed + one third-order step) and the integer
-// FP32<->FP64 conversions.  Prints one JSON object; tests/test_gpu_helpers.py
+// root (approximate seed + one third-order step), the integer FP32<->FP64
+// conversions and the FP64 comparisons on the integer pipes.  Prints one JSON object; tests/test_gpu_helpers.py
 // builds and runs it.  Every thread generates its own inputs from a
 // counter-based hash (splitmix64) and touches only the reduction words.
 #include <cstdio>
@@ -89,6 +89,35 @@ __global__ void check_narrow(unsigned long long* words, unsigned long long n) {
   atomicAdd(&words[5], nb);
 }
 
+// the FP64 comparisons on the integer pipes against the IEEE ones, on
+// random non-NaN patterns plus zeros of both signs, subnormals, infinities
+// and equal pairs (a pair of zeros of opposite sign is the one documented
+// difference of the ordered key and is skipped)
+__device__ bool is_nan(double x) { return x != x; }
+__global__ void check_compare(unsigned long long* words, unsigned long long n) {
+  unsigned long long nb = 0;
+  const double special[8] = {0.0, -0.0, 4.9e-324, -4.9e-324, 1.0 / 0.0, -1.0 / 0.0, 1.0, -1.0};
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long z = mix64(i + 12345);
+    double a = __longlong_as_double((long long)mix64(z));
+    double b = __longlong_as_double((long long)mix64(z + 7));
+    if ((z & 7) == 0) a = special[(z >> 3) & 7];
+    if ((z & 56) == 0) b = special[(z >> 6) & 7];
+    if ((z & 448) == 0) b = a;
+    if (is_nan(a) || is_nan(b)) continue;
+    nb += gt0(a) != (a > 0.0);
+    nb += lt0(a) != (a < 0.0);
+    if (a == 0.0 && b == 0.0) continue;
+    nb += lt_(a, b) != (a < b);
+    nb += le_(a, b) != (a <= b);
+    nb += rmin(a, b) != (a < b ? a : b);
+    nb += rmax(a, b) != (a > b ? a : b);
+    nb += rabs(a) != fabs(a);
+  }
+  atomicAdd(&words[6], nb);
+}
+
 int main() {
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
@@ -98,6 +127,7 @@ int main() {
   if (e == cudaSuccess) { check_math<<<nsm * 8, 256>>>(w, 1ull << 26); e = cudaGetLastError(); }
   if (e == cudaSuccess) { check_widen<<<nsm * 16, 256>>>(w); e = cudaGetLastError(); }
   if (e == cudaSuccess) { check_narrow<<<nsm * 16, 256>>>(w, 1ull << 31); e = cudaGetLastError(); }
+  if (e == cudaSuccess) { check_compare<<<nsm * 16, 256>>>(w, 1ull << 28); e = cudaGetLastError(); }
   unsigned long long h[8] = {0};
   if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof h, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
@@ -105,8 +135,8 @@ int main() {
     return 1;
   }
   printf("{\"rcp_max_rel\": %.6e, \"rsqrt_max_rel\": %.6e, \"sqrt_max_rel\": %.6e, \"special_mismatch\": %llu, "
-         "\"widen_mismatch\": %llu, \"narrow_mismatch\": %llu}\n",
+         "\"widen_mismatch\": %llu, \"narrow_mismatch\": %llu, \"compare_mismatch\": %llu}\n",
          __builtin_bit_cast(double, h[0]), __builtin_bit_cast(double, h[1]), __builtin_bit_cast(double, h[2]), h[3],
-         h[4], h[5]);
+         h[4], h[5], h[6]);
   return 0;
 }

@@ -7,7 +7,10 @@ operations (tests/cuda/helpers_check.cu, built here with nvcc):
   and NaN inputs;
 * the integer FP32<->FP64 conversions: bit-identical to the hardware
   conversions on every binary32 input and on 2^31 binary64 samples that
-  include every rounding tie and exponent edge."""
+  include every rounding tie and exponent edge;
+* the FP64 comparisons on the integer pipes (min, max, <, <=, sign tests,
+  abs): identical to the IEEE ones on 2^28 random non-NaN pairs with zeros,
+  subnormals, infinities and ties mixed in."""
 import json
 import os
 import subprocess
@@ -34,3 +37,4 @@ def test_arithmetic_helpers(tmp_path):
     assert r["special_mismatch"] == 0, r
     assert r["widen_mismatch"] == 0, r
     assert r["narrow_mismatch"] == 0, r
+    assert r["compare_mismatch"] == 0, r
