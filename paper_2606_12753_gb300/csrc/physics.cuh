@@ -139,18 +139,23 @@ __host__ __device__ __forceinline__ double fmin_(double a, double b) {
 }
 __host__ __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 
-// MC-limited slope of the middle of three values: with dm = q0 - qm and
-// dp = qp - q0, sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2) when dm and dp have the
-// same sign, else 0.  Doubling is exact, so 2 min(|dm|, |dp|) is the same
-// value as min(2|dm|, 2|dp|); a zero difference makes the minimum zero, so
-// only opposite signs need a test (which differs from testing dm dp > 0 only
-// when that product would underflow).
+// Half of the MC-limited slope of the middle of three values (a face takes
+// the cell value plus or minus it): with dm = q0 - qm and dp = qp - q0, the MC
+// slope is sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2) when dm and dp have the same
+// sign, else 0, and its half is sign(dp) min(|dm|, |dp|, |dm+dp|/4) -- the
+// same value exactly, since scaling by powers of two is exact.  A zero
+// difference makes the minimum zero, so only opposite signs need a test
+// (which differs from testing dm dp > 0 only when that product would
+// underflow).
 template <typename R>
-__host__ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
-  R dm = q0 - qm, dp = qp - q0;
-  R m = fmin_(R(2) * fmin_(rabs(dm), rabs(dp)), R(0.5) * rabs(dm + dp));
+__host__ __device__ __forceinline__ R mc_lim_half(R dm, R dp) {
+  R m = fmin_(fmin_(rabs(dm), rabs(dp)), R(0.25) * rabs(dm + dp));
   m = opposite_signs(dm, dp) ? R(0) : m;
   return copysign_(m, dp);
+}
+template <typename R>
+__host__ __device__ __forceinline__ R mc_half_slope(R qm, R q0, R qp) {
+  return mc_lim_half(q0 - qm, qp - q0);
 }
 
 // Fast magnetosonic speed along the normal; w = (rho, vn, vt1, vt2, p, Bt1,
@@ -235,15 +240,17 @@ __host__ __device__ __forceinline__ void hll_flux(const R* wl, const R* wr, R bn
   hll_flux_g(wl, wr, bn, gamma, R(1) / (gamma - R(1)), f, cmax);
 }
 
-// Star state of one side (Miyoshi & Kusano eqs. 43-48).
+// Star state of one side (Miyoshi & Kusano eqs. 43-48), with the outer
+// state's total energy, total pressure and v.B (its flux reuses them).
 template <typename R>
 struct Star {
   R rho, v, w, by, bz, e, vb, sq, isq;   // sq = sqrt(rho*), isq = 1/sqrt(rho*)
+  R eo, pto, vbo;
 };
 
 
 template <typename R>
-__host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, R s, R sm, R pts) {
+__host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, R pt, R s, R sm, R pts) {
   Star<R> st;
   R rho = w[0], u = w[1], v = w[2], ww = w[3], by = w[5], bz = w[6];
   R sd = s - u;
@@ -271,9 +278,11 @@ __host__ __device__ __forceinline__ Star<R> star_side(const R* w, R bn, R igm1, 
   st.rho = rho * sd * inv_ssm;
   R vb = u * bn + v * by + ww * bz;
   st.vb = sm * bn + st.v * st.by + st.w * st.bz;
-  R pt = w[4] + R(0.5) * (bn2 + by * by + bz * bz);
   R e = total_energy_i(w, bn, igm1);
   st.e = (sd * e - pt * u + pts * sm + bn * (vb - st.vb)) * inv_ssm;
+  st.eo = e;
+  st.pto = pt;
+  st.vbo = vb;
   st.isq = rrsqrt_(st.rho);
   st.sq = st.rho * st.isq;
   return st;
@@ -298,8 +307,8 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
   R sdl = sl - wl[1], sdr = sr - wr[1];
   R sm = (sdr * wr[0] * wr[1] - sdl * wl[0] * wl[1] - ptr + ptl) * rcp_(sdr * wr[0] - sdl * wl[0]);
   R pts = ptl + wl[0] * sdl * (sm - wl[1]);
-  Star<R> L = star_side(wl, bn, ig, sl, sm, pts);
-  Star<R> Rr = star_side(wr, bn, ig, sr, sm, pts);
+  Star<R> L = star_side(wl, bn, ig, ptl, sl, sm, pts);
+  Star<R> Rr = star_side(wr, bn, ig, ptr, sr, sm, pts);
   R abn = rabs(bn);
   R ssl = sm - abn * L.isq;
   R ssr = sm + abn * Rr.isq;
@@ -308,9 +317,20 @@ __host__ __device__ __forceinline__ void hlld_flux_g(const R* wl, const R* wr, R
   const Star<R>& S = left ? L : Rr;
   R so = left ? sl : sr;
   bool dbl = left ? lt0(ssl) : ge0(ssr);
+  // the outer state's flux and conserved values, from the energy, total
+  // pressure and v.B its star side already formed
   R fo[7];
-  phys_flux_i(w, bn, ig, fo);
-  R uo[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], total_energy_i(w, bn, ig), w[5], w[6]};
+  {
+    const R mu = w[0] * w[1];
+    fo[0] = mu;
+    fo[1] = mu * w[1] + S.pto - bn * bn;
+    fo[2] = mu * w[2] - bn * w[5];
+    fo[3] = mu * w[3] - bn * w[6];
+    fo[4] = (S.eo + S.pto) * w[1] - bn * S.vbo;
+    fo[5] = w[1] * w[5] - w[2] * bn;
+    fo[6] = w[1] * w[6] - w[3] * bn;
+  }
+  R uo[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], S.eo, w[5], w[6]};
   R us[7] = {S.rho, S.rho * sm, S.rho * S.v, S.rho * S.w, S.e, S.by, S.bz};
 #pragma unroll
   for (int q = 0; q < 7; ++q) f[q] = fo[q] + so * (us[q] - uo[q]);
@@ -366,16 +386,7 @@ __host__ __device__ __forceinline__ R edge_emf(R fa_m, R fa_p, R ma_m, R ma_p, R
   return avg + R(0.25) * (db_minus - db_plus) + R(0.25) * (da_minus - da_plus);
 }
 
-// MC limiter of a difference pair: sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2)
-// when dm and dp have the same sign, else 0.
-template <typename R>
-__host__ __device__ __forceinline__ R mc_lim(R dm, R dp) {
-  R m = fmin_(R(2) * fmin_(rabs(dm), rabs(dp)), R(0.5) * rabs(dm + dp));
-  m = opposite_signs(dm, dp) ? R(0) : m;
-  return copysign_(m, dp);
-}
-
-// Characteristic MC slope of the middle cell w0 of (wm, w0, wp), rotated
+// Half of the characteristic MC slope of the middle cell w0 of (wm, w0, wp), rotated
 // primitives (rho, v_n, v_t1, v_t2, p, B_t1, B_t2), bn0 the middle cell's
 // cell-centred normal field.  The one-sided differences are projected on the
 // left eigenvectors of the primitive Jacobian at w0, limited wave by wave and
@@ -385,7 +396,7 @@ __host__ __device__ __forceinline__ R mc_lim(R dm, R dp) {
 // both to the precision's degeneracy tolerance).  Each +/- wave pair shares
 // an even and an odd part of its projection, which the code forms once.
 template <typename R>
-__host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, const R* wp, R bn0, R gamma,
+__host__ __device__ __forceinline__ void char_half_slope(const R* wm, const R* w0, const R* wp, R bn0, R gamma,
                                                     R* slope) {
   const R rho = w0[0];
   const R ir = rcp_(rho);
@@ -422,7 +433,8 @@ __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, co
     as = R(0);
   }
   const R sg = ge0(bn0) ? R(1) : R(-1);
-  const R i2a2 = R(0.5) * rcp_(a2), i2r = i2a2 * ir, i2sa = R(0.5) * isr * rcp_(a), i2s = R(0.5) * isr;
+  const R ia2 = rcp_(a2);
+  const R i2a2 = R(0.5) * ia2, i2r = i2a2 * ir, i2sa = R(0.5) * isr * rcp_(a), i2s = R(0.5) * isr;
   R dc[7];   // limited wave amplitudes: f-, a-, s-, e, s+, a+, f+
   {
     R m[7], q[7];
@@ -440,13 +452,13 @@ __host__ __device__ __forceinline__ void char_slope(const R* wm, const R* w0, co
       c[0] = yf - xf;
       c[1] = ya - xa;
       c[2] = ys - xs;
-      c[3] = d[0] - d[4] / a2;
+      c[3] = d[0] - d[4] * ia2;
       c[4] = ys + xs;
       c[5] = ya + xa;
       c[6] = yf + xf;
     }
 #pragma unroll
-    for (int k = 0; k < 7; ++k) dc[k] = mc_lim(m[k], q[k]);
+    for (int k = 0; k < 7; ++k) dc[k] = mc_lim_half(m[k], q[k]);
   }
   const R Fp = dc[6] + dc[0], Fm = dc[6] - dc[0];
   const R Sp = dc[4] + dc[2], Sm = dc[4] - dc[2];
@@ -469,12 +481,12 @@ template <typename R>
 __host__ __device__ __forceinline__ void plm_face_char(const R* c0, const R* c1, const R* c2, const R* c3, R bn1,
                                                        R bn2, R gamma, R* wl, R* wr, R rho_floor, R p_floor) {
   R sl[7], sr_[7];
-  char_slope(c0, c1, c2, bn1, gamma, sl);
-  char_slope(c1, c2, c3, bn2, gamma, sr_);
+  char_half_slope(c0, c1, c2, bn1, gamma, sl);
+  char_half_slope(c1, c2, c3, bn2, gamma, sr_);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    wl[q] = c1[q] + R(0.5) * sl[q];
-    wr[q] = c2[q] - R(0.5) * sr_[q];
+    wl[q] = c1[q] + sl[q];
+    wr[q] = c2[q] - sr_[q];
   }
   wl[0] = rmax(wl[0], rho_floor);
   wr[0] = rmax(wr[0], rho_floor);
@@ -491,8 +503,8 @@ __host__ __device__ __forceinline__ void plm_face(const R* c0, const R* c1, cons
                                                   R rho_floor, R p_floor) {
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    wl[q] = c1[q] + R(0.5) * mc_slope(c0[q], c1[q], c2[q]);
-    wr[q] = c2[q] - R(0.5) * mc_slope(c1[q], c2[q], c3[q]);
+    wl[q] = c1[q] + mc_half_slope(c0[q], c1[q], c2[q]);
+    wr[q] = c2[q] - mc_half_slope(c1[q], c2[q], c3[q]);
   }
   wl[0] = rmax(wl[0], rho_floor);
   wr[0] = rmax(wr[0], rho_floor);

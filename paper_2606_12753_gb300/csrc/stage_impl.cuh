@@ -54,7 +54,7 @@ struct Tile {
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
   static constexpr int nI = W + H + 6;   // column/row maps, switch counters, the stage's dt
-  // per-cell slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
+  // per-cell half slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
   // x and y slopes of the current plane, z slopes of two planes (by parity)
   static constexpr int nSl = 7 * nZ;
   static constexpr int nSlope = 4 * nSl;
@@ -247,7 +247,7 @@ struct StageKernel {
   }
 
   // ------------------------------------------------------------- phase B0
-  // Slopes of plane q's cells over the (TX+2) x (TY+2) grid the faces touch:
+  // Half slopes of plane q's cells over the (TX+2) x (TY+2) grid the faces touch:
   // x and y (for the x-, y-faces of plane q) and z (for the z-faces on both
   // sides of plane q; kept by parity).  zonly: only the z slopes.
   static __device__ __forceinline__ void slopes(const Geo& g, R* sm, R* sl, int q, bool zonly) {
@@ -275,10 +275,10 @@ struct StageKernel {
         if (CHAR) bnc = Pq[7 * T::nR + r];
       }
       if (CHAR) {
-        char_slope(c[0], c[1], c[2], bnc, gam, out);
+        char_half_slope(c[0], c[1], c[2], bnc, gam, out);
       } else {
 #pragma unroll
-        for (int v = 0; v < 7; ++v) out[v] = mc_slope(c[0][v], c[1][v], c[2][v]);
+        for (int v = 0; v < 7; ++v) out[v] = mc_half_slope(c[0][v], c[1][v], c[2][v]);
       }
       R* dst = D == 0 ? sl : (D == 1 ? sl + T::nSl : sl + (2 + (q & 1)) * T::nSl);
 #pragma unroll
@@ -339,8 +339,8 @@ struct StageKernel {
       for (int v = 0; v < 7; ++v) {
         s1[v] = sa[v * n + ia];
         s2[v] = sb[v * n + ib];
-        wl[v] = c1[v] + R(0.5) * s1[v];
-        wr[v] = c2[v] - R(0.5) * s2[v];
+        wl[v] = c1[v] + s1[v];
+        wr[v] = c2[v] - s2[v];
       }
       wl[0] = rmax(wl[0], gpar<R>(g.rho_floor, g.frho_floor));
       wr[0] = rmax(wr[0], gpar<R>(g.rho_floor, g.frho_floor));
