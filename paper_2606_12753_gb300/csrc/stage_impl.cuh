@@ -173,15 +173,19 @@ struct StageKernel {
   static constexpr int W = T::W;
 
   // ---------------------------------------------------------------- phase A
+  // Threads [t0, blockDim.x) load, item r = threadIdx.x - t0 with stride
+  // blockDim.x - t0 (t0 > 0 leaves the threads of the update phase out).
   static __device__ __forceinline__ void load_plane(const Geo& g, const StageArgs& a, R* sm, const int* colc,
                                                     const int* rowc, double dt, int gi0, int gj0, int m,
-                                                    bool write_bn) {
+                                                    bool write_bn, int t0 = 0) {
     R* P = sm + T::oP + (m & 3) * 8 * T::nR;
     R* BN = sm + T::oBN + (m & 1) * 3 * T::nR;
     const bool zin = g.bc[2] == 0 || (m >= 0 && m < g.n[2]);
     const int ck = wrapc(m, g.n[2], g.bc[2]);
     const R* Win = (const R*)a.Win;
-    for (int r = threadIdx.x; r < T::nR; r += blockDim.x) {
+    const int t = (int)threadIdx.x - t0;
+    if (t < 0) return;
+    for (int r = t; r < T::nR; r += (int)blockDim.x - t0) {
       const int x = r % W, y = r / W;
       const int gi = gi0 - 2 + x, gj = gj0 - 2 + y;
       const bool inside = zin && (g.bc[0] == 0 || (gi >= 0 && gi < g.n[0])) &&
@@ -893,7 +897,9 @@ struct StageKernel {
     }
     __syncthreads();
     for (int k = kb - 1; k < ke; ++k) {
-      load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true);
+      // the threads without a cell in the update phase load the next plane
+      // while the others finish that phase
+      load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true, T::nC < (int)blockDim.x ? T::nC : 0);
       __syncthreads();
       if constexpr (SLOPES) {
         slopes(g, sm, sl, k + 1, false);
