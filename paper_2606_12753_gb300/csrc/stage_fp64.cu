@@ -9,8 +9,8 @@ cudaError_t launch_stage_fp64(int stage, int tx, int ty, unsigned nblocks, size_
                                  const Geo& g, const StageArgs& args) {
 #define X(TXv, TYv)                                                                              \
   if (tx == TXv && ty == TYv) {                                                                  \
-    if (stage == 1) stage_kernel<P_FP64, 1, TXv, TYv><<<nblocks, 256, smem, st>>>(g, args);     \
-    else stage_kernel<P_FP64, 2, TXv, TYv><<<nblocks, 256, smem, st>>>(g, args);                \
+    if (stage == 1) stage_kernel<P_FP64, 1, TXv, TYv><<<nblocks, stage_threads<P_FP64, TXv, TYv>(), smem, st>>>(g, args);     \
+    else stage_kernel<P_FP64, 2, TXv, TYv><<<nblocks, stage_threads<P_FP64, TXv, TYv>(), smem, st>>>(g, args);                \
     return cudaGetLastError();                                                                   \
   }
   MHD_TILES(X)
@@ -73,9 +73,9 @@ cudaError_t set_smem_learned_fp64(size_t bytes) {
 cudaError_t launch_stage_rk3_fp64(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
                                 const StageArgs& args) {
   if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
-  if (stage == ST_RK3_1) stage_kernel<P_FP64, ST_RK3_1, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
-  else if (stage == ST_RK3_2) stage_kernel<P_FP64, ST_RK3_2, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
-  else if (stage == ST_RK3_3) stage_kernel<P_FP64, ST_RK3_3, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
+  if (stage == ST_RK3_1) stage_kernel<P_FP64, ST_RK3_1, 16, 8><<<nblocks, stage_threads<P_FP64, 16, 8>(), smem, st>>>(g, args);
+  else if (stage == ST_RK3_2) stage_kernel<P_FP64, ST_RK3_2, 16, 8><<<nblocks, stage_threads<P_FP64, 16, 8>(), smem, st>>>(g, args);
+  else if (stage == ST_RK3_3) stage_kernel<P_FP64, ST_RK3_3, 16, 8><<<nblocks, stage_threads<P_FP64, 16, 8>(), smem, st>>>(g, args);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -920,8 +920,22 @@ struct StageKernel {
   }
 };
 
+// Threads per CTA and CTAs per SM of the plain stage kernel: FP64 tiles run
+// 256 threads (1 CTA per SM, 2 for 8x8); the FP32-bulk forms keep 24 warps
+// per SM at about 85 registers a thread: 3 CTAs of 256 threads for tiles of up
+// to 128 columns, 2 of 384 for 192 columns, 1 of 768 for 256 columns.
+template <int PREC, int TX, int TY>
+constexpr int stage_threads() {
+  return PREC == P_FP64 ? 256 : (TX * TY >= 256 ? 768 : (TX * TY >= 192 ? 384 : 256));
+}
+template <int PREC, int TX, int TY>
+constexpr int stage_min_blocks() {
+  return PREC == P_FP64 ? (TX * TY <= 64 ? 2 : 1) : 768 / stage_threads<PREC, TX, TY>();
+}
+
 template <int PREC, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(256, PREC == P_FP64 ? (TX * TY <= 64 ? 2 : 1) : 3) stage_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_blocks<PREC, TX, TY>())
+    stage_kernel(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY>::run_item(g, a, blockIdx.x, smem_raw);
 }
