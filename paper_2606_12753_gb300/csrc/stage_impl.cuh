@@ -161,7 +161,12 @@ constexpr bool slopes_in_smem() {
   return MODE == FM_CHAR || (PREC == P_FP64 && MODE == FM_PLAIN && TX * TY <= 128);
 }
 
-template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN>
+// SPLIT: the update phase splits each cell between two threads (face group
+// and conserved group, named-barrier hand-over); the CTA then needs at least
+// two threads per cell of a plane.  Measured faster for the mixed and FP64
+// forms, slower for FP32 (its update phase carries no FP64 work) and for the
+// batch kernel.
+template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false>
 struct StageKernel {
   static constexpr bool LEARN = MODE == FM_LEARNED;
   static constexpr bool CHAR = MODE == FM_CHAR;
@@ -712,10 +717,21 @@ struct StageKernel {
   // with identical arithmetic) and its five conserved values, stores the
   // faces it owns (its lower faces, and the top face of an outflow axis),
   // then recovers its primitives from its own new faces.  No face values pass
-  // through shared memory, so no barrier separates faces from cells.
-  static __device__ __forceinline__ void update_plane(const Geo& g, const StageArgs& a, R* sm, const StepDt& dt,
-                                                      int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
-                                                      bool& bad, R& smax) {
+  // through shared memory, so no barrier of the whole CTA separates faces
+  // from cells.
+  // When the CTA has two threads per cell, the work of a cell is split
+  // between them: thread c (face group) advances the faces and recovers the
+  // primitives; thread nC + c (conserved group) advances the five conserved
+  // values, hands them over in shared memory (the flux arrays, idle in this
+  // phase) and signals a named barrier without waiting on it, then goes on to
+  // load the next plane.  The face group waits on that barrier before its
+  // recovery.
+  static constexpr int kUpdateBarrier = 1;   // named barrier of the hand-over (0 is __syncthreads)
+
+  // advance of the six faces of cell (i, j) of plane k; stores the owned ones
+  static __device__ __forceinline__ void advance_faces(const Geo& g, const StageArgs& a, const R* sm,
+                                                       const StepDt& dt, int i, int j, int gi, int gj, int k,
+                                                       double (&b)[6]) {
     const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]),
             idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
     const R* EZ = sm + T::oEZ;
@@ -723,62 +739,116 @@ struct StageKernel {
     const R* EY0 = EX0 + T::nE;
     const R* EX1 = sm + T::oEXY + ((k + 1) & 1) * 2 * T::nE;   // k+1/2
     const R* EY1 = EX1 + T::nE;
-    const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
-    R* Wout = (R*)a.Wout;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const bool outx = g.bc[0] == 1, outy = g.bc[1] == 1, outz = g.bc[2] == 1;
-    for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
+    const int e = i + (TX + 1) * j;            // edge/face slot of the cell's lower corner
+    // increments of the six faces
+    const R lx0 = -((EZ[e + (TX + 1)] - EZ[e]) * idy - (EY1[e] - EY0[e]) * idz);
+    const R lx1 = -((EZ[e + 1 + (TX + 1)] - EZ[e + 1]) * idy - (EY1[e + 1] - EY0[e + 1]) * idz);
+    const R ly0 = -((EX1[e] - EX0[e]) * idz - (EZ[e + 1] - EZ[e]) * idx);
+    const R ly1 = -((EX1[e + (TX + 1)] - EX0[e + (TX + 1)]) * idz -
+                    (EZ[e + 1 + (TX + 1)] - EZ[e + (TX + 1)]) * idx);
+    const R lz0 = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
+    const R lz1 = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
+    // their global indices (periodic axes wrap the top face to 0)
+    const long long fx0 = xface_index(g, gi, gj, k);
+    const long long fx1 = xface_index(g, gi + 1 == nx && !outx ? 0 : gi + 1, gj, k);
+    const long long fy0 = yface_index(g, gi, gj, k);
+    const long long fy1 = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
+    const long long fz0 = zface_index(g, gi, gj, k);
+    const long long fz1 = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
+    const S bx0 = advance(a, fx0, lx0, dt), bx1 = advance(a, fx1, lx1, dt);
+    const S by0 = advance(a, fy0, ly0, dt), by1 = advance(a, fy1, ly1, dt);
+    const S bz0 = advance(a, fz0, lz0, dt), bz1 = advance(a, fz1, lz1, dt);
+    emit(a, fx0, lx0, bx0);
+    emit(a, fy0, ly0, by0);
+    emit(a, fz0, lz0, bz0);
+    if (outx && gi + 1 == nx) emit(a, fx1, lx1, bx1);
+    if (outy && gj + 1 == ny) emit(a, fy1, ly1, by1);
+    if (outz && k + 1 == nz) emit(a, fz1, lz1, bz1);
+    b[0] = (double)bx0; b[1] = (double)bx1; b[2] = (double)by0;
+    b[3] = (double)by1; b[4] = (double)bz0; b[5] = (double)bz1;
+  }
+
+  // advance of the five conserved values of cell c (global index s)
+  static __device__ __forceinline__ void advance_cell(const Geo& g, const StageArgs& a, const R* DU, const StepDt& dt,
+                                                      int c, long long s, double (&u)[5]) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const R l = DU[v * T::nC + c];
+      const S nv = advance(a, v * g.ncell + s, l, dt);
+      emit(a, v * g.ncell + s, l, nv);
+      u[v] = (double)nv;
+    }
+  }
+
+  // primitives, their store, counters and the CFL speed of one cell
+  static __device__ __forceinline__ void recover_cell(const Geo& g, const StageArgs& a, long long s,
+                                                      const double (&u)[5], const double (&b)[6], unsigned& nrho,
+                                                      unsigned& np, bool& bad, R& smax) {
+    R* Wout = (R*)a.Wout;
+    R w[NW];
+    int hr, hp;
+    recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], b[0], b[1], b[2], b[3], b[4], b[5], w, hr, hp);
+    nrho += hr;
+    np += hp;
+    if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
+#pragma unroll
+    for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
+    if (StageTraits<STAGE>::last) {
+      const R sp = cfl_speed<R>(g, w);
+      smax = sp > smax ? sp : smax;
+    }
+  }
+
+  static __device__ __forceinline__ void update_plane(const Geo& g, const StageArgs& a, R* sm, const StepDt& dt,
+                                                      int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
+                                                      bool& bad, R& smax) {
+    const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
+    const int nx = g.n[0], ny = g.n[1];
+    const int t = threadIdx.x;
+    if constexpr (SPLIT) {
+      static_assert(T::nC % 32 == 0, "the split update phase needs whole warps per group");
+      double* U5 = reinterpret_cast<double*>(sm + T::oHX);   // [5][nC], in the idle flux arrays
+      static_assert((size_t)5 * T::nC * sizeof(double) <= (size_t)5 * (T::nX + T::nY + T::nZ) * sizeof(R),
+                    "hand-over does not fit in the flux arrays");
+      if (t >= 2 * T::nC) return;
+      const int c = t < T::nC ? t : t - T::nC;
+      const int i = c % TX, j = c / TX;
+      const int gi = gi0 + i, gj = gj0 + j;
+      const bool valid = gi < nx && gj < ny;
+      const long long s = (long long)gi + (long long)nx * ((long long)gj + (long long)ny * k);
+      if (t >= T::nC) {   // conserved group: advance, hand over, do not wait
+        if (valid) {
+          double u[5];
+          advance_cell(g, a, DU, dt, c, s, u);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U5[v * T::nC + c] = u[v];
+        }
+        asm volatile("bar.arrive %0, %1;" ::"r"(kUpdateBarrier), "r"(2 * T::nC) : "memory");
+        return;
+      }
+      double b[6];
+      if (valid) advance_faces(g, a, sm, dt, i, j, gi, gj, k, b);
+      asm volatile("bar.sync %0, %1;" ::"r"(kUpdateBarrier), "r"(2 * T::nC) : "memory");
+      if (!valid || !a.Wout) return;   // no Wout: operator evaluation only (mhd_rhs)
+      double u[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = U5[v * T::nC + c];
+      recover_cell(g, a, s, u, b, nrho, np, bad, smax);
+      return;
+    } else {
+    for (int c = t; c < T::nC; c += blockDim.x) {
       const int i = c % TX, j = c / TX;
       const int gi = gi0 + i, gj = gj0 + j;
       if (gi >= nx || gj >= ny) continue;
-      const int e = i + (TX + 1) * j;            // edge/face slot of the cell's lower corner
-      // increments of the six faces
-      const R lx0 = -((EZ[e + (TX + 1)] - EZ[e]) * idy - (EY1[e] - EY0[e]) * idz);
-      const R lx1 = -((EZ[e + 1 + (TX + 1)] - EZ[e + 1]) * idy - (EY1[e + 1] - EY0[e + 1]) * idz);
-      const R ly0 = -((EX1[e] - EX0[e]) * idz - (EZ[e + 1] - EZ[e]) * idx);
-      const R ly1 = -((EX1[e + (TX + 1)] - EX0[e + (TX + 1)]) * idz -
-                      (EZ[e + 1 + (TX + 1)] - EZ[e + (TX + 1)]) * idx);
-      const R lz0 = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
-      const R lz1 = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
-      // their global indices (periodic axes wrap the top face to 0)
-      const long long fx0 = xface_index(g, gi, gj, k);
-      const long long fx1 = xface_index(g, gi + 1 == nx && !outx ? 0 : gi + 1, gj, k);
-      const long long fy0 = yface_index(g, gi, gj, k);
-      const long long fy1 = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
-      const long long fz0 = zface_index(g, gi, gj, k);
-      const long long fz1 = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
-      const S bx0 = advance(a, fx0, lx0, dt), bx1 = advance(a, fx1, lx1, dt);
-      const S by0 = advance(a, fy0, ly0, dt), by1 = advance(a, fy1, ly1, dt);
-      const S bz0 = advance(a, fz0, lz0, dt), bz1 = advance(a, fz1, lz1, dt);
-      emit(a, fx0, lx0, bx0);
-      emit(a, fy0, ly0, by0);
-      emit(a, fz0, lz0, bz0);
-      if (outx && gi + 1 == nx) emit(a, fx1, lx1, bx1);
-      if (outy && gj + 1 == ny) emit(a, fy1, ly1, by1);
-      if (outz && k + 1 == nz) emit(a, fz1, lz1, bz1);
       const long long s = (long long)gi + (long long)nx * ((long long)gj + (long long)ny * k);
-      double u[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const R l = DU[v * T::nC + c];
-        const S nv = advance(a, v * g.ncell + s, l, dt);
-        emit(a, v * g.ncell + s, l, nv);
-        u[v] = (double)nv;
-      }
+      double b[6], u[5];
+      advance_faces(g, a, sm, dt, i, j, gi, gj, k, b);
+      advance_cell(g, a, DU, dt, c, s, u);
       if (!a.Wout) continue;   // operator evaluation only (mhd_rhs)
-      R w[NW];
-      int hr, hp;
-      recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], (double)bx0, (double)bx1, (double)by0, (double)by1,
-                    (double)bz0, (double)bz1, w, hr, hp);
-      nrho += hr;
-      np += hp;
-      if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
-#pragma unroll
-      for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
-      if (StageTraits<STAGE>::last) {
-        const R sp = cfl_speed<R>(g, w);
-        smax = sp > smax ? sp : smax;
-      }
+      recover_cell(g, a, s, u, b, nrho, np, bad, smax);
+    }
     }
   }
 
@@ -925,19 +995,24 @@ struct StageKernel {
 // per SM at about 85 registers a thread: 3 CTAs of 256 threads for tiles of up
 // to 128 columns, 2 of 384 for 192 columns, 1 of 768 for 256 columns.
 template <int PREC, int TX, int TY>
-constexpr int stage_threads() {
+__host__ __device__ constexpr int stage_threads() {
   return PREC == P_FP64 ? 256 : (TX * TY >= 256 ? 768 : (TX * TY >= 192 ? 384 : 256));
 }
 template <int PREC, int TX, int TY>
-constexpr int stage_min_blocks() {
+__host__ __device__ constexpr int stage_min_blocks() {
   return PREC == P_FP64 ? (TX * TY <= 64 ? 2 : 1) : 768 / stage_threads<PREC, TX, TY>();
+}
+
+template <int PREC, int TX, int TY>
+__host__ __device__ constexpr bool stage_split() {
+  return PREC != P_FP32 && (TX * TY) % 32 == 0 && 2 * TX * TY <= stage_threads<PREC, TX, TY>();
 }
 
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_blocks<PREC, TX, TY>())
     stage_kernel(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY>::run_item(g, a, blockIdx.x, smem_raw);
+  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>()>::run_item(g, a, blockIdx.x, smem_raw);
 }
 
 // The same stage with the learned HLL/HLLD face switch.
@@ -951,7 +1026,8 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_lear
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_CHAR>::run_item(g, a, blockIdx.x, smem_raw);
+  StageKernel<PREC, STAGE, TX, TY, FM_CHAR, PREC != P_FP32 && 2 * TX * TY <= 256>::run_item(g, a, blockIdx.x,
+                                                                                            smem_raw);
 }
 
 // Primitives (and the CFL max) of a state set from outside: one thread per cell.
