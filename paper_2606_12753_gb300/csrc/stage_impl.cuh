@@ -728,10 +728,20 @@ struct StageKernel {
   // recovery.
   static constexpr int kUpdateBarrier = 1;   // named barrier of the hand-over (0 is __syncthreads)
 
+  // The upper z-face of a cell at plane k is its lower z-face at plane k+1,
+  // advanced with the same arithmetic; a thread that keeps its cell column
+  // from plane to plane carries it (value and increment) instead of
+  // advancing it again.
+  struct ZCarry {
+    S v;
+    R l;
+    bool have;
+  };
+
   // advance of the six faces of cell (i, j) of plane k; stores the owned ones
   static __device__ __forceinline__ void advance_faces(const Geo& g, const StageArgs& a, const R* sm,
                                                        const StepDt& dt, int i, int j, int gi, int gj, int k,
-                                                       double (&b)[6]) {
+                                                       double (&b)[6], ZCarry* zc = nullptr) {
     const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]),
             idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
     const R* EZ = sm + T::oEZ;
@@ -748,7 +758,8 @@ struct StageKernel {
     const R ly0 = -((EX1[e] - EX0[e]) * idz - (EZ[e + 1] - EZ[e]) * idx);
     const R ly1 = -((EX1[e + (TX + 1)] - EX0[e + (TX + 1)]) * idz -
                     (EZ[e + 1 + (TX + 1)] - EZ[e + (TX + 1)]) * idx);
-    const R lz0 = -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
+    const bool carried = zc && zc->have;
+    const R lz0 = carried ? zc->l : -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
     const R lz1 = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
     // their global indices (periodic axes wrap the top face to 0)
     const long long fx0 = xface_index(g, gi, gj, k);
@@ -759,7 +770,12 @@ struct StageKernel {
     const long long fz1 = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
     const S bx0 = advance(a, fx0, lx0, dt), bx1 = advance(a, fx1, lx1, dt);
     const S by0 = advance(a, fy0, ly0, dt), by1 = advance(a, fy1, ly1, dt);
-    const S bz0 = advance(a, fz0, lz0, dt), bz1 = advance(a, fz1, lz1, dt);
+    const S bz0 = carried ? zc->v : advance(a, fz0, lz0, dt), bz1 = advance(a, fz1, lz1, dt);
+    if (zc) {
+      zc->v = bz1;
+      zc->l = lz1;
+      zc->have = true;
+    }
     emit(a, fx0, lx0, bx0);
     emit(a, fy0, ly0, by0);
     emit(a, fz0, lz0, bz0);
@@ -801,9 +817,11 @@ struct StageKernel {
     }
   }
 
+  // zc: the face group's z-face carry (split form; reset at a chunk's
+  // first plane)
   static __device__ __forceinline__ void update_plane(const Geo& g, const StageArgs& a, R* sm, const StepDt& dt,
                                                       int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
-                                                      bool& bad, R& smax) {
+                                                      bool& bad, R& smax, ZCarry& zc) {
     const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
     const int nx = g.n[0], ny = g.n[1];
     const int t = threadIdx.x;
@@ -829,7 +847,7 @@ struct StageKernel {
         return;
       }
       double b[6];
-      if (valid) advance_faces(g, a, sm, dt, i, j, gi, gj, k, b);
+      if (valid) advance_faces(g, a, sm, dt, i, j, gi, gj, k, b, &zc);
       asm volatile("bar.sync %0, %1;" ::"r"(kUpdateBarrier), "r"(2 * T::nC) : "memory");
       if (!valid || !a.Wout) return;   // no Wout: operator evaluation only (mhd_rhs)
       double u[5];
@@ -948,7 +966,8 @@ struct StageKernel {
       __syncthreads();
       edges_2d(g, sm);
       __syncthreads();
-      update_plane(g, a, sm, sdt, gi0, gj0, 0, nrho, np, bad, smax);
+      ZCarry zc{S(0), R(0), false};
+      update_plane(g, a, sm, sdt, gi0, gj0, 0, nrho, np, bad, smax, zc);
       finish(a, nrho, np, nh, nd, bad, smax);
       return;
     }
@@ -966,6 +985,7 @@ struct StageKernel {
       fluxes(g, sm, kb - 2, kb - 1, false);
     }
     __syncthreads();
+    ZCarry zc{S(0), R(0), false};   // face group: upper z-face of the previous plane
     for (int k = kb - 1; k < ke; ++k) {
       // the threads without a cell in the update phase load the next plane
       // while the others finish that phase
@@ -983,7 +1003,7 @@ struct StageKernel {
       __syncthreads();
       divergence_and_edges(g, sm, k);
       __syncthreads();
-      if (k >= kb) update_plane(g, a, sm, sdt, gi0, gj0, k, nrho, np, bad, smax);
+      if (k >= kb) update_plane(g, a, sm, sdt, gi0, gj0, k, nrho, np, bad, smax, zc);
     }
 
     finish(a, nrho, np, nh, nd, bad, smax);
