@@ -1039,7 +1039,8 @@ __global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_block
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_learned(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_LEARNED>::run_item(g, a, blockIdx.x, smem_raw);
+  StageKernel<PREC, STAGE, TX, TY, FM_LEARNED, PREC != P_FP32 && 2 * TX * TY <= 256>::run_item(g, a, blockIdx.x,
+                                                                                               smem_raw);
 }
 
 // The same stage with characteristic reconstruction.
