@@ -80,7 +80,7 @@ def parse():
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--tile", default="0,0,0")
     p.add_argument("--compare-steps", type=int, default=10)
-    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--e2e-steps", type=int, default=40)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
     p.add_argument("--recon", default="primitive", choices=["primitive", "characteristic"],

@@ -144,16 +144,16 @@ int mhd_step(mhd_handle* h, double dt, int nsteps);
  * of (cell_in, face_in) to the device on the handle's input copy stream, one
  * step of it (dt as in mhd_step: dt <= 0 takes the CFL dt of that input) on
  * the handle's stream, and the copy of the result to (cell_out, face_out) on
- * its output copy stream, and returns.  Consecutive calls alternate between
- * two input and two output device slots, so the copies of one state overlap
- * the step of the next: with pinned host buffers a stream of states runs at
- * the rate of the slowest of the three (host-to-device, step,
+ * its output copy stream, and returns.  Consecutive calls rotate over three
+ * input and three output device slots, so the copies of one state overlap
+ * the steps of its neighbours: with pinned host buffers a stream of states
+ * runs at the rate of the slowest of the three (host-to-device, step,
  * device-to-host) instead of their sum.  Arrays are laid out as in
  * mhd_set_state, element type as the state (FP32 in MHD_FP32, else FP64).
  * Ownership: every host buffer passed since the last mhd_stream_sync must
  * stay valid and unmodified, and outputs must not be read, until
  * mhd_stream_sync returns; no other call may use the handle in between.  The
- * first call allocates two extra device states.  After mhd_stream_sync the
+ * first call allocates four extra device states.  After mhd_stream_sync the
  * handle's current state is the last result.  Errors: MHD_ERR_INVALID (null
  * pointers, NaN dt, learned switch without a network), MHD_ERR_NOMEM,
  * MHD_ERR_CUDA; mhd_stream_sync also returns MHD_ERR_NONFINITE when a step met

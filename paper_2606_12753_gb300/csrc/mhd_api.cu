@@ -172,10 +172,11 @@ struct mhd_handle {
   // U pointers rotate over them), the two input slots, the copy streams and
   // the events that order slot reuse between the three streams
   std::vector<void*> owned_states;
-  void* slot_in[2] = {nullptr, nullptr};
-  void* slot_out[2] = {nullptr, nullptr};
+  static constexpr int kSlots = 3;         // device states in flight per direction
+  void* slot_in[kSlots] = {};
+  void* slot_out[kSlots] = {};
   cudaStream_t s_in = nullptr, s_out = nullptr;
-  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
+  cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
   long long nstream = 0;                   // streamed steps since the handle was created
 };
 
@@ -372,7 +373,7 @@ extern "C" void mhd_destroy(mhd_handle* h) {
   if (h->s_in) cudaStreamSynchronize(h->s_in);
   if (h->s_out) cudaStreamSynchronize(h->s_out);
   for (void* p : h->owned_states) cudaFree(p);
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < mhd_handle::kSlots; ++p) {
     if (h->ev_h2d[p]) cudaEventDestroy(h->ev_h2d[p]);
     if (h->ev_comp[p]) cudaEventDestroy(h->ev_comp[p]);
     if (h->ev_d2h[p]) cudaEventDestroy(h->ev_d2h[p]);
@@ -574,14 +575,21 @@ static int stream_setup(mhd_handle* h) {
   if (h->s_in) return MHD_OK;
   const size_t bytes = (size_t)h->geo.total * h->elem;
   cudaError_t e = cudaSuccess;
-  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+  constexpr int NS = mhd_handle::kSlots;
+  for (int p = 0; p < NS && e == cudaSuccess; ++p) {
     e = cudaMalloc(&h->slot_in[p], bytes);
     if (e == cudaSuccess) h->owned_states.push_back(h->slot_in[p]);
   }
-  // the output slots are the handle's own state buffers
-  h->slot_out[0] = h->owned_states[0];
-  h->slot_out[1] = h->owned_states[1];
-  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+  // the output slots: the handle's own two state buffers and further ones
+  for (int p = 0; p < NS && e == cudaSuccess; ++p) {
+    if (p < 2) {
+      h->slot_out[p] = h->owned_states[p];
+    } else {
+      e = cudaMalloc(&h->slot_out[p], bytes);
+      if (e == cudaSuccess) h->owned_states.push_back(h->slot_out[p]);
+    }
+  }
+  for (int p = 0; p < NS && e == cudaSuccess; ++p) {
     e = cudaEventCreateWithFlags(&h->ev_h2d[p], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[p], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_d2h[p], cudaEventDisableTiming);
@@ -624,7 +632,7 @@ extern "C" int mhd_stream_step(mhd_handle* h, const void* const cell_in[5], cons
   if (dt != dt) return fail(h, MHD_ERR_INVALID, "dt is NaN");
   if (int rc = need_switch(h)) return rc;
   if (int rc = stream_setup(h)) return rc;
-  const int p = (int)(h->nstream & 1);
+  const int p = (int)(h->nstream % mhd_handle::kSlots);
   // input: slot p is free once the step that read it (two back) has run
   CUDA_TRY(h, cudaStreamWaitEvent(h->s_in, h->ev_comp[p], 0));
   CUDA_TRY(h, copy_state_async(h, true, (char*)h->slot_in[p], (void* const*)cell_in, (void* const*)face_in, h->s_in));
