@@ -47,7 +47,8 @@ size_t smem_bytes_fp32(int tx, int ty) {
 size_t smem_bytes_char_fp32() { return Tile<16, 8>::bytes<Prec<P_FP32>::R, Prec<P_FP32>::S, true>(); }
 
 cudaError_t launch_prims_fp32(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
-  prims_kernel<P_FP32><<<nblocks, 256, 0, st>>>(g, args);
+  (void)nblocks;   // one CTA per (j, k) row of cells
+  prims_kernel<P_FP32><<<(unsigned)((long long)g.n[1] * g.n[2]), 128, 0, st>>>(g, args);
   return cudaGetLastError();
 }
 

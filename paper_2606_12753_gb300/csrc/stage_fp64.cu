@@ -47,7 +47,8 @@ size_t smem_bytes_fp64(int tx, int ty) {
 size_t smem_bytes_char_fp64() { return Tile<16, 8>::bytes<Prec<P_FP64>::R, Prec<P_FP64>::S, true>(); }
 
 cudaError_t launch_prims_fp64(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
-  prims_kernel<P_FP64><<<nblocks, 256, 0, st>>>(g, args);
+  (void)nblocks;   // one CTA per (j, k) row of cells
+  prims_kernel<P_FP64><<<(unsigned)((long long)g.n[1] * g.n[2]), 128, 0, st>>>(g, args);
   return cudaGetLastError();
 }
 

@@ -122,24 +122,6 @@ __device__ __forceinline__ double face_value(const Geo& g, const StageArgs& a, d
   return f0 + (double)fr.t * (f1 - f0);
 }
 
-// Primitives of an interior cell from the conserved state of the stage's
-// input (U^n in stage 1, U^n + dt K1 in stage 2) and its own faces.
-template <int PREC, int STAGE>
-__device__ void cell_prims(const Geo& g, const StageArgs& a, double dt, int i, int j, int k,
-                           typename Prec<PREC>::R* w, int& rho_hit, int& p_hit) {
-  const long long s = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
-  double u[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) u[v] = cons_at<PREC, STAGE>(a, v * g.ncell + s, dt);
-  const double bxl = face_value<PREC, STAGE>(g, a, dt, 0, i, j, k, i);
-  const double bxh = face_value<PREC, STAGE>(g, a, dt, 0, i, j, k, i + 1);
-  const double byl = face_value<PREC, STAGE>(g, a, dt, 1, i, j, k, j);
-  const double byh = face_value<PREC, STAGE>(g, a, dt, 1, i, j, k, j + 1);
-  const double bzl = face_value<PREC, STAGE>(g, a, dt, 2, i, j, k, k);
-  const double bzh = face_value<PREC, STAGE>(g, a, dt, 2, i, j, k, k + 1);
-  recover<PREC>(g, u[0], u[1], u[2], u[3], u[4], bxl, bxh, byl, byh, bzl, bzh, w, rho_hit, p_hit);
-}
-
 // Step size of a stage in the forms its updates use: dt and dt/2 in FP64 and
 // rounded to FP32.
 struct StepDt {
@@ -1051,21 +1033,36 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char
                                                                                             smem_raw);
 }
 
-// Primitives (and the CFL max) of a state set from outside: one thread per cell.
+// Primitives (and the CFL max) of a state set from outside.  One CTA per
+// (j, k) row of cells, threads along x: the row's index math is one division
+// per CTA, and a cell's faces are its own (the face above the last cell of a
+// periodic axis is face 0), so no ghost logic is needed.
 template <int PREC>
-__global__ void __launch_bounds__(256) prims_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
   using R = typename Prec<PREC>::R;
+  using S = typename Prec<PREC>::S;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const long long row = blockIdx.x;             // j + ny k
+  const int j = (int)(row % ny), k = (int)(row / ny);
+  const int jh = j + 1 < g.nf[1] ? j + 1 : 0, kh = k + 1 < g.nf[2] ? k + 1 : 0;
+  const S* U = (const S*)a.U;
+  R* Wout = (R*)a.Wout;
+  const long long ybase_lo = g.face_off[1] + (long long)nx * (j + (long long)g.nf[1] * k);
+  const long long ybase_hi = g.face_off[1] + (long long)nx * (jh + (long long)g.nf[1] * k);
+  const long long zbase_lo = g.face_off[2] + (long long)nx * (j + (long long)ny * k);
+  const long long zbase_hi = g.face_off[2] + (long long)nx * (j + (long long)ny * kh);
+  const long long xbase = g.face_off[0] + (long long)g.nf[0] * row;
   R smax = R(0);
   bool bad = false;
-  R* Wout = (R*)a.Wout;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.ncell;
-       s += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(s % g.n[0]);
-    const int j = (int)((s / g.n[0]) % g.n[1]);
-    const int k = (int)(s / ((long long)g.n[0] * g.n[1]));
+  (void)nz;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const long long s = i + (long long)nx * row;
+    const int ih = i + 1 < g.nf[0] ? i + 1 : 0;
     R w[NW];
     int hr, hp;
-    cell_prims<PREC, 1>(g, a, 0.0, i, j, k, w, hr, hp);
+    recover<PREC>(g, (double)U[s], (double)U[g.ncell + s], (double)U[2 * g.ncell + s], (double)U[3 * g.ncell + s],
+                  (double)U[4 * g.ncell + s], (double)U[xbase + i], (double)U[xbase + ih], (double)U[ybase_lo + i],
+                  (double)U[ybase_hi + i], (double)U[zbase_lo + i], (double)U[zbase_hi + i], w, hr, hp);
     if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
 #pragma unroll
     for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];

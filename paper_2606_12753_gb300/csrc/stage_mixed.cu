@@ -47,7 +47,8 @@ size_t smem_bytes_mixed(int tx, int ty) {
 size_t smem_bytes_char_mixed() { return Tile<16, 8>::bytes<Prec<P_MIXED>::R, Prec<P_MIXED>::S, true>(); }
 
 cudaError_t launch_prims_mixed(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
-  prims_kernel<P_MIXED><<<nblocks, 256, 0, st>>>(g, args);
+  (void)nblocks;   // one CTA per (j, k) row of cells
+  prims_kernel<P_MIXED><<<(unsigned)((long long)g.n[1] * g.n[2]), 128, 0, st>>>(g, args);
   return cudaGetLastError();
 }
 
