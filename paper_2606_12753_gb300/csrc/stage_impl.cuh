@@ -13,9 +13,11 @@
 //      and on the x- and y-faces of plane k+1 (one halo row across, for the
 //      edge EMFs), and the cell-centred EMF -v x B of plane k+1;
 //   C  flux divergence and the Gardiner-Stone edge EMFs E_z(k), E_x, E_y(k+1/2);
-//   D  new face values (-curl E), then per owned cell the new conserved state,
-//      its primitives (FP64 pressure recovery in the FP64/mixed forms) and,
-//      in the last stage of a step, the CFL speed of U^{n+1}.
+//   D  per cell of plane k: its six new face values (-curl E; the faces it
+//      owns are stored), its new conserved state, its primitives (FP64
+//      pressure recovery in the FP64/mixed forms) and, in the last stage of a
+//      step, the CFL speed of U^{n+1}; meanwhile the threads without a cell
+//      load the next plane (phase A of plane k+1).
 // This is the chain Reconstruct -> HLLD_Solver -> RightHandSide -> CT_EMF ->
 // US of the paper's MHD step (Sec. 2.2, Table 2) fused into one pass per
 // RK stage.
@@ -133,7 +135,7 @@ struct StepDt {
 // learned HLL/HLLD switch, characteristic reconstruction.
 enum { FM_PLAIN = 0, FM_LEARNED = 1, FM_CHAR = 2 };
 
-// Whether a stage kernel computes each cell's slopes once per plane into
+// Whether a stage kernel computes each cell's half slopes once per plane into
 // shared memory (a slope phase before the flux phase) instead of once per
 // face that uses it: FP64 on tiles of up to 128 columns (the FP64 pipe bounds
 // it and the slopes fit beside the ring without costing occupancy) and
