@@ -240,16 +240,26 @@ class ClockSampler:
                 "timed_s": round(self.t1 - self.t0, 3)}
 
 
-def traffic_from_profiles(kernel_tag):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.txt for this
-    kernel, if the kernel sources are unchanged since the capture."""
-    from paper_2606_12753_gb300 import _build
+def kernel_source_digest() -> str:
+    """Hash of the CUDA sources with comments and blank space removed, so that
+    only a change of the code itself invalidates a recorded capture."""
     import hashlib
+    import re
+    from paper_2606_12753_gb300 import _build
     h = hashlib.sha1()
     for p in _build._deps():
         if p.endswith((".cu", ".cuh")):
-            h.update(open(p, "rb").read())
-    digest = h.hexdigest()[:12]
+            src = open(p, encoding="utf-8").read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
+            h.update(" ".join(src.split()).encode())
+    return h.hexdigest()[:12]
+
+
+def traffic_from_profiles(kernel_tag):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.txt for this
+    kernel, if the kernel code is unchanged since the capture."""
+    digest = kernel_source_digest()
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         for line in open(path):
