@@ -32,6 +32,10 @@ template <> struct Prec<P_FP64> { using S = double; using R = double; using K = 
 template <> struct Prec<P_MIXED> { using S = double; using R = float; using K = float; };
 template <> struct Prec<P_FP32> { using S = float; using R = float; using K = float; };
 
+// type A if C, else B
+template <bool C, class A, class B> struct Pick { using type = A; };
+template <class A, class B> struct Pick<false, A, B> { using type = B; };
+
 // status bits
 enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 // counters

@@ -150,7 +150,7 @@ constexpr bool slopes_in_smem() {
 // two threads per cell of a plane.  Measured faster for the mixed and FP64
 // forms, slower for FP32 (its update phase carries no FP64 work) and for the
 // batch kernel.
-template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false>
+template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false>
 struct StageKernel {
   static constexpr bool LEARN = MODE == FM_LEARNED;
   static constexpr bool CHAR = MODE == FM_CHAR;
@@ -647,37 +647,59 @@ struct StageKernel {
     }
   }
 
+  // The stored values one new value is formed from: RK2 U^n (a) and, in
+  // stage 2, K1 (b); RK3 the stage's input state (a) and, after its first
+  // stage, U^n (b).
+  struct Old {
+    S a;
+    typename Pick<StageTraits<STAGE>::rk3, S, K>::type b;
+  };
+  static __device__ __forceinline__ Old fetch(const StageArgs& a, long long gidx) {
+    Old o;
+    if (StageTraits<STAGE>::rk3) {
+      o.a = ((const S*)a.Uin)[gidx];
+      o.b = STAGE == ST_RK3_1 ? S(0) : ((const S*)a.U)[gidx];
+    } else {
+      o.a = ((const S*)a.U)[gidx];
+      o.b = STAGE == ST_RK2_1 ? K(0) : ((const K*)a.K1)[gidx];
+    }
+    return o;
+  }
+
   // new value of one conserved quantity from its increment l:
   // RK2 stage 1 U* = U^n + dt K1 (K1 = l rounded to K), stage 2 U^n + dt/2 (K1 + l);
   // RK3 (input state U_in): U1 = U_in + dt l, U2 = 3/4 U^n + 1/4 (U_in + dt l),
   // U^{n+1} = 1/3 U^n + 2/3 (U_in + dt l)
-  static __device__ __forceinline__ S advance(const StageArgs& a, long long gidx, R l, const StepDt& t) {
+  static __device__ __forceinline__ S advance(const Old& o, R l, const StepDt& t) {
     if (StageTraits<STAGE>::rk3) {
-      const S ui = ((const S*)a.Uin)[gidx];
+      const S ui = o.a;
       if (PREC == P_FP32) {
         const float e = ui + t.fdt * l;
         if (STAGE == ST_RK3_1) return e;
-        const float un = ((const S*)a.U)[gidx];
+        const float un = o.b;
         if (STAGE == ST_RK3_2) return 0.75f * un + 0.25f * e;
         return un / 3.0f + 2.0f / 3.0f * e;
       }
       const double e = fma(t.dt, to_f64(l), (double)ui);
       if (STAGE == ST_RK3_1) return (S)e;
-      const double un = (double)((const S*)a.U)[gidx];
+      const double un = (double)o.b;
       if (STAGE == ST_RK3_2) return (S)(0.75 * un + 0.25 * e);
       return (S)((1.0 / 3.0) * un + (2.0 / 3.0) * e);
     }
-    const S un = ((const S*)a.U)[gidx];
+    const S un = o.a;
     if (STAGE == 1) {
       const K k1 = (K)l;
       if (PREC == P_FP32) return un + t.fdt * k1;
       return (S)fma(t.dt, to_f64(k1), (double)un);
     } else {
-      const K k1 = ((const K*)a.K1)[gidx];
+      const K k1 = o.b;
       if (PREC == P_FP32) return un + t.fhdt * (k1 + l);
       if (PREC == P_MIXED) return fma(t.hdt, to_f64(k1 + l), (double)un);
       return (S)((double)un + t.hdt * ((double)k1 + (double)l));
     }
+  }
+  static __device__ __forceinline__ S advance(const StageArgs& a, long long gidx, R l, const StepDt& t) {
+    return advance(fetch(a, gidx), l, t);
   }
 
   static __device__ __forceinline__ void emit(const StageArgs& a, long long gidx, R l, S v) {
@@ -722,10 +744,25 @@ struct StageKernel {
     bool have;
   };
 
-  // advance of the six faces of cell (i, j) of plane k; stores the owned ones
+  // global indices of the six faces of cell (gi, gj, k) in the order
+  // x-, x+, y-, y+, z-, z+ (periodic axes wrap the top face to 0)
+  static __device__ __forceinline__ void face_indices(const Geo& g, int gi, int gj, int k, long long (&f)[6]) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const bool outx = g.bc[0] == 1, outy = g.bc[1] == 1, outz = g.bc[2] == 1;
+    f[0] = xface_index(g, gi, gj, k);
+    f[1] = xface_index(g, gi + 1 == nx && !outx ? 0 : gi + 1, gj, k);
+    f[2] = yface_index(g, gi, gj, k);
+    f[3] = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
+    f[4] = zface_index(g, gi, gj, k);
+    f[5] = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
+  }
+
+  // advance of the six faces of cell (i, j) of plane k; stores the owned ones.
+  // pre: the faces' stored values, fetched ahead (nullptr: fetched here)
   static __device__ __forceinline__ void advance_faces(const Geo& g, const StageArgs& a, const R* sm,
                                                        const StepDt& dt, int i, int j, int gi, int gj, int k,
-                                                       double (&b)[6], ZCarry* zc = nullptr) {
+                                                       double (&b)[6], ZCarry* zc = nullptr,
+                                                       const Old* pre = nullptr) {
     const R idx = gpar<R>(g.inv_d[0], g.finv_d[0]), idy = gpar<R>(g.inv_d[1], g.finv_d[1]),
             idz = gpar<R>(g.inv_d[2], g.finv_d[2]);
     const R* EZ = sm + T::oEZ;
@@ -752,9 +789,12 @@ struct StageKernel {
     const long long fy1 = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
     const long long fz0 = zface_index(g, gi, gj, k);
     const long long fz1 = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
-    const S bx0 = advance(a, fx0, lx0, dt), bx1 = advance(a, fx1, lx1, dt);
-    const S by0 = advance(a, fy0, ly0, dt), by1 = advance(a, fy1, ly1, dt);
-    const S bz0 = carried ? zc->v : advance(a, fz0, lz0, dt), bz1 = advance(a, fz1, lz1, dt);
+    const S bx0 = pre ? advance(pre[0], lx0, dt) : advance(a, fx0, lx0, dt);
+    const S bx1 = pre ? advance(pre[1], lx1, dt) : advance(a, fx1, lx1, dt);
+    const S by0 = pre ? advance(pre[2], ly0, dt) : advance(a, fy0, ly0, dt);
+    const S by1 = pre ? advance(pre[3], ly1, dt) : advance(a, fy1, ly1, dt);
+    const S bz0 = carried ? zc->v : pre ? advance(pre[4], lz0, dt) : advance(a, fz0, lz0, dt);
+    const S bz1 = pre ? advance(pre[5], lz1, dt) : advance(a, fz1, lz1, dt);
     if (zc) {
       zc->v = bz1;
       zc->l = lz1;
@@ -771,12 +811,13 @@ struct StageKernel {
   }
 
   // advance of the five conserved values of cell c (global index s)
+  // (pre: their stored values, fetched ahead; nullptr: fetched here)
   static __device__ __forceinline__ void advance_cell(const Geo& g, const StageArgs& a, const R* DU, const StepDt& dt,
-                                                      int c, long long s, double (&u)[5]) {
+                                                      int c, long long s, double (&u)[5], const Old* pre = nullptr) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const R l = DU[v * T::nC + c];
-      const S nv = advance(a, v * g.ncell + s, l, dt);
+      const S nv = pre ? advance(pre[v], l, dt) : advance(a, v * g.ncell + s, l, dt);
       emit(a, v * g.ncell + s, l, nv);
       u[v] = (double)nv;
     }
@@ -801,11 +842,44 @@ struct StageKernel {
     }
   }
 
+  // Split form with PREFETCH: the stored values each thread of the update
+  // phase reads (face thread: its six faces, the lower z-face only when not
+  // carried; conserved-value thread: its five values) are loaded into
+  // registers before phase C, so that the loads are in flight while the
+  // edges are formed.  Chosen for kernels with registers to spare (plain
+  // FP64, characteristic reconstruction); in the kernels capped at 80 or 128
+  // registers (FP32-bulk, learned switch) the held values spill, and a
+  // cp.async copy into the idle ring slot measured slower there too.
+  static constexpr bool kPF = SPLIT && PREFETCH;
+  struct Pre {
+    Old o[6];
+  };
+  static __device__ __forceinline__ void prefetch(const Geo& g, const StageArgs& a, int gi0, int gj0, int k,
+                                                  bool carried, Pre& p) {
+    const int t = threadIdx.x;
+    if (t >= 2 * T::nC) return;
+    const int c = t < T::nC ? t : t - T::nC;
+    const int gi = gi0 + c % TX, gj = gj0 + c / TX;
+    if (gi >= g.n[0] || gj >= g.n[1]) return;
+    if (t >= T::nC) {
+      const long long s = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) p.o[v] = fetch(a, v * g.ncell + s);
+    } else {
+      long long f[6];
+      face_indices(g, gi, gj, k, f);
+#pragma unroll
+      for (int m = 0; m < 6; ++m)
+        if (m != 4 || !carried) p.o[m] = fetch(a, f[m]);
+    }
+  }
+
   // zc: the face group's z-face carry (split form; reset at a chunk's
-  // first plane)
+  // first plane); pre: the values prefetch() fetched for this plane (nullptr:
+  // none were)
   static __device__ __forceinline__ void update_plane(const Geo& g, const StageArgs& a, R* sm, const StepDt& dt,
                                                       int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
-                                                      bool& bad, R& smax, ZCarry& zc) {
+                                                      bool& bad, R& smax, ZCarry& zc, const Pre* pre = nullptr) {
     const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
     const int nx = g.n[0], ny = g.n[1];
     const int t = threadIdx.x;
@@ -823,7 +897,7 @@ struct StageKernel {
       if (t >= T::nC) {   // conserved group: advance, hand over, do not wait
         if (valid) {
           double u[5];
-          advance_cell(g, a, DU, dt, c, s, u);
+          advance_cell(g, a, DU, dt, c, s, u, pre ? pre->o : nullptr);
 #pragma unroll
           for (int v = 0; v < 5; ++v) U5[v * T::nC + c] = u[v];
         }
@@ -831,7 +905,7 @@ struct StageKernel {
         return;
       }
       double b[6];
-      if (valid) advance_faces(g, a, sm, dt, i, j, gi, gj, k, b, &zc);
+      if (valid) advance_faces(g, a, sm, dt, i, j, gi, gj, k, b, &zc, pre ? pre->o : nullptr);
       asm volatile("bar.sync %0, %1;" ::"r"(kUpdateBarrier), "r"(2 * T::nC) : "memory");
       if (!valid || !a.Wout) return;   // no Wout: operator evaluation only (mhd_rhs)
       double u[5];
@@ -985,9 +1059,13 @@ struct StageKernel {
         fluxes(g, sm, k, k + 1, true);
       }
       __syncthreads();
+      Pre pre;
+      if constexpr (kPF) {
+        if (k >= kb) prefetch(g, a, gi0, gj0, k, zc.have, pre);
+      }
       divergence_and_edges(g, sm, k);
       __syncthreads();
-      if (k >= kb) update_plane(g, a, sm, sdt, gi0, gj0, k, nrho, np, bad, smax, zc);
+      if (k >= kb) update_plane(g, a, sm, sdt, gi0, gj0, k, nrho, np, bad, smax, zc, kPF ? &pre : nullptr);
     }
 
     finish(a, nrho, np, nh, nd, bad, smax);
@@ -1016,7 +1094,8 @@ template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_blocks<PREC, TX, TY>())
     stage_kernel(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>()>::run_item(g, a, blockIdx.x, smem_raw);
+  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>(), PREC == P_FP64>::run_item(g, a, blockIdx.x,
+                                                                                                    smem_raw);
 }
 
 // The same stage with the learned HLL/HLLD face switch.
@@ -1031,8 +1110,8 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_lear
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char(Geo g, StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_CHAR, PREC != P_FP32 && 2 * TX * TY <= 256>::run_item(g, a, blockIdx.x,
-                                                                                            smem_raw);
+  StageKernel<PREC, STAGE, TX, TY, FM_CHAR, PREC != P_FP32 && 2 * TX * TY <= 256, true>::run_item(g, a, blockIdx.x,
+                                                                                                   smem_raw);
 }
 
 // Primitives (and the CFL max) of a state set from outside.  One CTA per
