@@ -12,7 +12,9 @@
 //      (HLLD / HLL, or the learned choice between them) on the z-faces k+1/2
 //      and on the x- and y-faces of plane k+1 (one halo row across, for the
 //      edge EMFs), and the cell-centred EMF -v x B of plane k+1;
-//   C  flux divergence and the Gardiner-Stone edge EMFs E_z(k), E_x, E_y(k+1/2);
+//   C  flux divergence and the Gardiner-Stone edge EMFs E_z(k), E_x, E_y(k+1/2)
+//      (kernels with registers to spare first issue the loads of phase D's
+//      stored values, so that they complete during this phase);
 //   D  per cell of plane k: its six new face values (-curl E; the faces it
 //      owns are stored), its new conserved state, its primitives (FP64
 //      pressure recovery in the FP64/mixed forms) and, in the last stage of a
@@ -149,7 +151,8 @@ constexpr bool slopes_in_smem() {
 // and conserved group, named-barrier hand-over); the CTA then needs at least
 // two threads per cell of a plane.  Measured faster for the mixed and FP64
 // forms, slower for FP32 (its update phase carries no FP64 work) and for the
-// batch kernel.
+// batch kernel.  PREFETCH (split form only): phase D's stored values are
+// loaded into registers before phase C.
 template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false>
 struct StageKernel {
   static constexpr bool LEARN = MODE == FM_LEARNED;
