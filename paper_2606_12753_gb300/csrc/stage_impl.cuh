@@ -747,17 +747,17 @@ struct StageKernel {
     bool have;
   };
 
-  // global indices of the six faces of cell (gi, gj, k) in the order
-  // x-, x+, y-, y+, z-, z+ (periodic axes wrap the top face to 0)
-  static __device__ __forceinline__ void face_indices(const Geo& g, int gi, int gj, int k, long long (&f)[6]) {
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const bool outx = g.bc[0] == 1, outy = g.bc[1] == 1, outz = g.bc[2] == 1;
-    f[0] = xface_index(g, gi, gj, k);
-    f[1] = xface_index(g, gi + 1 == nx && !outx ? 0 : gi + 1, gj, k);
-    f[2] = yface_index(g, gi, gj, k);
-    f[3] = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
-    f[4] = zface_index(g, gi, gj, k);
-    f[5] = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
+  // global index of face m of cell (gi, gj, k), m = 0..5 for x-, x+, y-, y+,
+  // z-, z+ (periodic axes wrap the top face to 0)
+  static __device__ __forceinline__ long long face_index(const Geo& g, int gi, int gj, int k, int m) {
+    switch (m) {
+      case 0: return xface_index(g, gi, gj, k);
+      case 1: return xface_index(g, gi + 1 == g.n[0] && g.bc[0] != 1 ? 0 : gi + 1, gj, k);
+      case 2: return yface_index(g, gi, gj, k);
+      case 3: return yface_index(g, gi, gj + 1 == g.n[1] && g.bc[1] != 1 ? 0 : gj + 1, k);
+      case 4: return zface_index(g, gi, gj, k);
+      default: return zface_index(g, gi, gj, k + 1 == g.n[2] && g.bc[2] != 1 ? 0 : k + 1);
+    }
   }
 
   // advance of the six faces of cell (i, j) of plane k; stores the owned ones.
@@ -785,13 +785,9 @@ struct StageKernel {
     const bool carried = zc && zc->have;
     const R lz0 = carried ? zc->l : -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
     const R lz1 = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
-    // their global indices (periodic axes wrap the top face to 0)
-    const long long fx0 = xface_index(g, gi, gj, k);
-    const long long fx1 = xface_index(g, gi + 1 == nx && !outx ? 0 : gi + 1, gj, k);
-    const long long fy0 = yface_index(g, gi, gj, k);
-    const long long fy1 = yface_index(g, gi, gj + 1 == ny && !outy ? 0 : gj + 1, k);
-    const long long fz0 = zface_index(g, gi, gj, k);
-    const long long fz1 = zface_index(g, gi, gj, k + 1 == nz && !outz ? 0 : k + 1);
+    const long long fx0 = face_index(g, gi, gj, k, 0), fx1 = face_index(g, gi, gj, k, 1);
+    const long long fy0 = face_index(g, gi, gj, k, 2), fy1 = face_index(g, gi, gj, k, 3);
+    const long long fz0 = face_index(g, gi, gj, k, 4), fz1 = face_index(g, gi, gj, k, 5);
     const S bx0 = pre ? advance(pre[0], lx0, dt) : advance(a, fx0, lx0, dt);
     const S bx1 = pre ? advance(pre[1], lx1, dt) : advance(a, fx1, lx1, dt);
     const S by0 = pre ? advance(pre[2], ly0, dt) : advance(a, fy0, ly0, dt);
@@ -869,11 +865,9 @@ struct StageKernel {
 #pragma unroll
       for (int v = 0; v < 5; ++v) p.o[v] = fetch(a, v * g.ncell + s);
     } else {
-      long long f[6];
-      face_indices(g, gi, gj, k, f);
 #pragma unroll
       for (int m = 0; m < 6; ++m)
-        if (m != 4 || !carried) p.o[m] = fetch(a, f[m]);
+        if (m != 4 || !carried) p.o[m] = fetch(a, face_index(g, gi, gj, k, m));
     }
   }
 
