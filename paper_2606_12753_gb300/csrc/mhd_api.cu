@@ -597,8 +597,23 @@ static int stream_setup(mhd_handle* h) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    // undo this call's allocations, so that a later call starts afresh
     int code = e == cudaErrorMemoryAllocation ? MHD_ERR_NOMEM : MHD_ERR_CUDA;
     cudaGetLastError();
+    for (int p = 0; p < NS; ++p) {
+      if (h->ev_h2d[p]) cudaEventDestroy(h->ev_h2d[p]);
+      if (h->ev_comp[p]) cudaEventDestroy(h->ev_comp[p]);
+      if (h->ev_d2h[p]) cudaEventDestroy(h->ev_d2h[p]);
+      h->ev_h2d[p] = h->ev_comp[p] = h->ev_d2h[p] = nullptr;
+      h->slot_in[p] = h->slot_out[p] = nullptr;
+    }
+    if (h->s_out) cudaStreamDestroy(h->s_out);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    h->s_out = h->s_in = nullptr;
+    while (h->owned_states.size() > 2) {   // the first two are the handle's own state buffers
+      cudaFree(h->owned_states.back());
+      h->owned_states.pop_back();
+    }
     return fail(h, code, "streaming setup failed: %s", cudaGetErrorString(e));
   }
   return MHD_OK;

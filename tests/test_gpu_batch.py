@@ -34,17 +34,17 @@ def load_batch(boxes, precision, tile=(8, 8, 8)):
 
 def test_batch_fp64_matches_oracle_with_per_box_cfl_dt():
     boxes = small_blasts()
-    b = load_batch(boxes, "fp64")
-    for i, bx in enumerate(boxes):
-        assert b.box_dt(i) == pytest.approx(O.cfl_dt(ocfg(bx), bx.cell, bx.face), rel=1e-13)
-    b.step(-1.0, 3)
-    for i, bx in enumerate(boxes):
-        rc, rf, _ = O.step(ocfg(bx), bx.cell, bx.face, -1.0, nsteps=3)
-        c, f = b.get_state(i)
-        errs = state_errors(c, f, rc, rf)
-        assert max(errs.values()) <= 1e-12, (i, bx.name, errs)
-    assert b.stats()["status"] == 0
-    b.close()
+    with load_batch(boxes, "fp64") as b:
+        for i, bx in enumerate(boxes):
+            assert b.box_dt(i) == pytest.approx(O.cfl_dt(ocfg(bx), bx.cell, bx.face), rel=1e-13)
+        b.step(-1.0, 3)
+        for i, bx in enumerate(boxes):
+            rc, rf, _ = O.step(ocfg(bx), bx.cell, bx.face, -1.0, nsteps=3)
+            c, f = b.get_state(i)
+            errs = state_errors(c, f, rc, rf)
+            assert max(errs.values()) <= 1e-12, (i, bx.name, errs)
+        assert b.stats()["status"] == 0
+    assert b.h is None   # the batch is destroyed on leaving the block
 
 
 def _kappa(box):

@@ -18,13 +18,13 @@ TOL = {"fp64": 1e-12, "mixed": 1e-5, "fp32": 1e-5}
 
 def run_gpu(box, dts, precision="fp64", **kw):
     from paper_2606_12753_gb300 import mhd
-    s = mhd.Solver(box, precision=precision, **kw)
-    s.set_state(box.cell, box.face)
-    for dt in dts:
-        s.step(dt, 1)
-    c, f = s.get_state()
-    st = s.stats()
-    s.close()
+    with mhd.Solver(box, precision=precision, **kw) as s:
+        s.set_state(box.cell, box.face)
+        for dt in dts:
+            s.step(dt, 1)
+        c, f = s.get_state()
+        st = s.stats()
+    assert s.h is None   # the handle is destroyed on leaving the block
     return c, f, st
 
 
