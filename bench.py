@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -168,7 +169,8 @@ class ClockSampler:
         self.interval_ms = interval_ms
         self.proc = None
         self.t0 = self.t1 = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        out = os.environ.get("MHD_CLOCKS_DIR") or tempfile.gettempdir()   # where the raw samples go
+        self.path = os.path.join(out, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -614,7 +616,6 @@ def run_ours(args):
 def run_batch(args):
     """64 independent outflow blast boxes advanced by one persistent launch
     per call (all K timed steps in one launch, replayed from a CUDA graph)."""
-    import tempfile
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
