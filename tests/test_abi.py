@@ -136,3 +136,53 @@ def test_char_recon_validation():
         cfgs[k].recon = mhd.MHD_RECON_CHARACTERISTIC
     h = mhd.C.c_void_p()
     assert mhd.load().mhd_batch_create(2, cfgs, None, mhd.C.byref(h)) == mhd.MHD_ERR_INVALID
+
+
+def test_null_handles_and_arguments_are_rejected():
+    """Every entry point that takes a handle answers a null one (or null
+    output pointers) with MHD_ERR_INVALID on the host, before any CUDA call,
+    and the destroy calls accept null."""
+    from paper_2606_12753_gb300 import _build
+    L = C.CDLL(_build.LIB)   # a separate instance: plain ctypes arguments
+    P, I, D = C.c_void_p(None), C.c_int, C.c_double
+    calls = {
+        "mhd_set_state": (P, P, P, I(0)),
+        "mhd_get_state": (P, P, P, I(0)),
+        "mhd_step": (P, D(1e-3), I(1)),
+        "mhd_step_async": (P, D(1e-3), I(1)),
+        "mhd_stream_step": (P, P, P, P, P, D(1e-3)),
+        "mhd_stream_sync": (P,),
+        "mhd_set_profiling": (P, I(1)),
+        "mhd_get_profile": (P, P, P),
+        "mhd_rhs": (P, P, P, I(0)),
+        "mhd_cfl_dt": (P, P),
+        "mhd_divb_max": (P, P),
+        "mhd_get_stats": (P, P),
+        "mhd_dump_faces": (P, P, C.c_longlong(0), P, P, P),
+        "mhd_set_switch": (P, P, D(0.5)),
+        "mhd_switch_choices": (P, P, P),
+        "mhd_batch_set_state": (P, I(0), P, P, I(0)),
+        "mhd_batch_get_state": (P, I(0), P, P, I(0)),
+        "mhd_batch_step": (P, D(-1.0), I(1)),
+        "mhd_batch_step_async": (P, D(-1.0), I(1)),
+        "mhd_batch_set_tile": (P, I(16), I(8), I(8)),
+        "mhd_batch_get_tile": (P, P, P, P),
+        "mhd_batch_autotune": (P, I(1), C.c_char_p(None), P, P),
+        "mhd_batch_set_barrier_timeout": (P, D(1.0)),
+        "mhd_batch_inject_missed_arrival": (P, I(1)),
+        "mhd_batch_box_dt": (P, I(0), P),
+        "mhd_batch_get_stats": (P, P),
+        "mhd_create": (P, P, P),
+        "mhd_batch_create": (I(1), P, P, P),
+        "mhd_measure_pipe_peaks": (P, P),
+    }
+    for name, args in calls.items():
+        f = getattr(L, name)
+        f.restype = C.c_int
+        assert f(*args) == mhd.MHD_ERR_INVALID, name
+    L.mhd_destroy(P)
+    L.mhd_batch_destroy(P)
+    L.mhd_last_error.restype = C.c_char_p
+    L.mhd_batch_last_error.restype = C.c_char_p
+    assert L.mhd_last_error(P) is not None
+    assert L.mhd_batch_last_error(P) is not None
