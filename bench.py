@@ -91,6 +91,21 @@ def parse():
     return p.parse_args()
 
 
+SLOWDOWNS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_disqualify(clocks) -> bool:
+    """Whether a timed run's clock samples rule it out: a hardware or thermal
+    slowdown, or an SM clock well below its maximum with no reason given (a
+    clock lock left behind).  A power cap alone does not (a 1.4 kW part under
+    a dense load); no samples cannot decide either way."""
+    if not clocks:
+        return False
+    if set(clocks["reasons"]) & set(SLOWDOWNS):
+        return True
+    return not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]
+
+
 def max_over_ranks(value: float, world: int, device="cuda") -> float:
     """MAX of a per-rank float over all ranks of the process group (one
     collective; the timing rule takes the slowest rank)."""
@@ -410,25 +425,37 @@ def run_ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    clk = ClockSampler(local).start()
-    solver.step_async(-1.0, args.warmup)
-    st_w = solver.stats()
-    solver.set_profiling(True)
-    solver.profile()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
+    def timed_once():
+        """W warm-up steps, then K steps timed with CUDA events on the
+        solver's stream, clocks sampled throughout."""
+        clk = ClockSampler(local).start()
+        solver.step_async(-1.0, args.warmup)
+        st_w = solver.stats()
+        solver.set_profiling(True)
+        solver.profile()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clk.mark_start()
+        e0.record(stream)
+        solver.step_async(-1.0, args.steps)
+        e1.record(stream)
+        stream.synchronize()
+        clk.mark_end()
+        clk.stop()
+        barrier()
+        stage_ms, launches = solver.profile()
+        solver.set_profiling(False)
+        return e0.elapsed_time(e1), stage_ms, launches, clk.summary(), st_w
+
+    ms_total, stage_ms, launches, clocks, st_w = timed_once()
+    if max_over_ranks(1.0 if clocks_disqualify(clocks) else 0.0, world) > 0:
+        first = clocks   # measured once more; the first run's clocks are kept for the record
+        ms_total, stage_ms, launches, clocks, st_w = timed_once()
+        if clocks is not None:
+            clocks["remeasured_after"] = first
+    e0 = torch.cuda.Event(enable_timing=True)   # for the comparison legs below
     e1 = torch.cuda.Event(enable_timing=True)
-    clk.mark_start()
-    e0.record(stream)
-    solver.step_async(-1.0, args.steps)
-    e1.record(stream)
-    stream.synchronize()
-    clk.mark_end()
-    clk.stop()
-    barrier()
-    ms_total = e0.elapsed_time(e1)
-    stage_ms, launches = solver.profile()
-    solver.set_profiling(False)
     st = solver.stats()
     if st["status"] != 0:
         raise RuntimeError(f"device status {st['status']} after the timed steps")
@@ -604,7 +631,6 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
     elif rank == 0:
         out["e2e"] = None
-    clocks = clk.summary()
     out["clocks"] = clocks
     solver.close()
     if rank == 0:
@@ -638,20 +664,29 @@ def run_batch(args):
         batch.set_state(i, b.cell, b.face)
     cache = os.environ.get("MHD_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "mhd_autotune.jsonl")
     tile, tune_ms = batch.autotune(trial_steps=3, cache_path=cache)
-    clk = ClockSampler(local).start()
-    batch.step(-1.0, args.warmup)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    clk.mark_start()
-    e0.record(stream)
-    batch.step_async(-1.0, args.steps)
-    e1.record(stream)
-    stream.synchronize()
-    clk.mark_end()
-    clk.stop()
-    barrier()
-    ms_total = max_over_ranks(e0.elapsed_time(e1), world)
+    def timed_once():
+        clk = ClockSampler(local).start()
+        batch.step(-1.0, args.warmup)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clk.mark_start()
+        e0.record(stream)
+        batch.step_async(-1.0, args.steps)
+        e1.record(stream)
+        stream.synchronize()
+        clk.mark_end()
+        clk.stop()
+        barrier()
+        return e0.elapsed_time(e1), clk.summary()
+
+    ms_local, clocks = timed_once()
+    if max_over_ranks(1.0 if clocks_disqualify(clocks) else 0.0, world) > 0:
+        first = clocks
+        ms_local, clocks = timed_once()
+        if clocks is not None:
+            clocks["remeasured_after"] = first
+    ms_total = max_over_ranks(ms_local, world)
     st = batch.stats()
     if st["status"] != 0:
         raise RuntimeError(f"device status {st['status']} after the timed steps")
@@ -674,7 +709,7 @@ def run_batch(args):
                      "peak_kind": peak_kind},
         "gpu_launches": 2 if args.steps else 0,
         "e2e": None,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     batch.close()
     if rank == 0:

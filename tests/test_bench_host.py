@@ -76,3 +76,13 @@ def test_traffic_lookup_follows_the_current_sources():
         assert value is not None and value > 0
     else:
         assert value is None
+
+
+def test_clocks_disqualify():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_disqualify(ok)
+    assert not bench.clocks_disqualify(None)
+    assert not bench.clocks_disqualify({**ok, "sm_mhz": 1700.0, "reasons": ["sw_power_cap"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_disqualify({**ok, "reasons": [r]})
+    assert bench.clocks_disqualify({**ok, "sm_mhz": 1400.0})   # well below maximum, no reason: a clock lock
