@@ -91,6 +91,8 @@ def parse():
     return p.parse_args()
 
 
+# instruction issue: one warp-instruction per clock per scheduler, 4 schedulers per SM
+ISSUE_PEAK_WARP_INST_PER_S = SMS * 4 * SM_MAX_GHZ * 1e9
 SLOWDOWNS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 
 
@@ -273,19 +275,25 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:12]
 
 
-def traffic_from_profiles(kernel_tag):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.txt for this
-    kernel, if the kernel code is unchanged since the capture."""
+def profile_record(kernel_tag):
+    """The fields profiles/traffic.txt records for this kernel (ncu counts per
+    launch), if the kernel code is unchanged since the capture; else None."""
     digest = kernel_source_digest()
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         for line in open(path):
             f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if f.get("kernel") == kernel_tag and f.get("src") == digest:
-                return float(f["dram_bytes_per_launch"]), digest
+                return f, digest
     except FileNotFoundError:
         pass
     return None, digest
+
+
+def traffic_from_profiles(kernel_tag):
+    """ncu DRAM bytes per launch recorded for this kernel (None when stale)."""
+    rec, digest = profile_record(kernel_tag)
+    return (float(rec["dram_bytes_per_launch"]) if rec else None), digest
 
 
 def cpu_oracle_rate(seconds: float, n: int = 64):
@@ -493,6 +501,17 @@ def run_ours(args):
         "stage_ms_per_launch": [stage_ms[i] / max(launches[i], 1) for i in range(nst)],
         "gpu_launches": nst * args.steps,
     }
+    # the same kernel against the SM's instruction-issue rate, from the
+    # executed warp-instructions ncu recorded for it (null once stale)
+    rec, _ = profile_record(tag)
+    out["roofline_issue"] = None
+    if rec and "warp_inst_per_launch" in rec:
+        inst = float(rec["warp_inst_per_launch"])
+        rate = inst / (per_launch_ms / 1e3)
+        out["roofline_issue"] = {"bound": "issue", "achieved": rate / 1e9, "peak": ISSUE_PEAK_WARP_INST_PER_S / 1e9,
+                                 "unit": "G warp-instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST_PER_S,
+                                 "kernel": tag, "warp_instructions_per_launch": inst,
+                                 "source": "ncu smsp__inst_executed.sum (profiles/traffic.txt)"}
     out["pipes"] = pipe_report(args, box, value / world, measured)
     if out["pipes"] is not None:
         out["pipes"]["measured_peaks"] = measured

@@ -4,6 +4,8 @@ kernel-source digest and the traffic lookup keyed by it."""
 import datetime
 import os
 
+import pytest
+
 import bench
 
 
@@ -86,3 +88,10 @@ def test_clocks_disqualify():
     for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
         assert bench.clocks_disqualify({**ok, "reasons": [r]})
     assert bench.clocks_disqualify({**ok, "sm_mhz": 1400.0})   # well below maximum, no reason: a clock lock
+
+
+def test_profile_record_carries_the_instruction_count():
+    rec, digest = bench.profile_record("stage_kernel<mixed,2>@turbulence_3d_256")
+    if rec is not None:   # captured for the current sources
+        assert float(rec["warp_inst_per_launch"]) > 0 and float(rec["dram_bytes_per_launch"]) > 0
+    assert bench.ISSUE_PEAK_WARP_INST_PER_S == pytest.approx(152 * 4 * 2.07e9)
