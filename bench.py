@@ -260,8 +260,9 @@ class ClockSampler:
 
 
 def kernel_source_digest() -> str:
-    """Hash of the CUDA sources with comments and blank space removed, so that
-    only a change of the code itself invalidates a recorded capture."""
+    """Hash of the CUDA sources with comments and blank space removed, and of
+    the compiler flags (without machine paths), so that only a change of what
+    is compiled invalidates a recorded capture."""
     import hashlib
     import re
     from paper_2606_12753_gb300 import _build
@@ -272,6 +273,9 @@ def kernel_source_digest() -> str:
             src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
             src = re.sub(r"//[^\n]*", " ", src)
             h.update(" ".join(src.split()).encode())
+    flags = [x for x in _build.ARCH + _build.NVCC_FLAGS if not os.path.isabs(x)]
+    flags += _build.FAST_FP32_FLAGS + sorted(_build.FAST_FP32_UNITS)
+    h.update(" ".join(flags).encode())
     return h.hexdigest()[:12]
 
 

@@ -64,6 +64,13 @@ def test_source_digest_ignores_comments(tmp_path, monkeypatch):
     assert bench.kernel_source_digest() == d0
     a.write_text("int f() { return 2; }\n")
     assert bench.kernel_source_digest() != d0
+    a.write_text("int f() { return 1; }\n")
+    assert bench.kernel_source_digest() == d0
+    monkeypatch.setattr(_build, "FAST_FP32_FLAGS", [])     # the same source compiled differently
+    assert bench.kernel_source_digest() != d0
+    monkeypatch.setattr(_build, "FAST_FP32_FLAGS", ["-prec-div=false", "-prec-sqrt=false"])
+    monkeypatch.setattr(_build, "NVCC_FLAGS", [x if x != _build.CSRC else "/elsewhere/csrc" for x in _build.NVCC_FLAGS])
+    assert bench.kernel_source_digest() == d0                # machine paths do not count
 
 
 def test_traffic_lookup_follows_the_current_sources():
