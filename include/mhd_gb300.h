@@ -11,7 +11,7 @@
  *     cell field B_c the mean of the cell's two staggered faces;
  *   - piecewise-linear reconstruction of (rho, v, p, B_t) with the MC limiter,
  *     on the primitives or (MHD_RECON_CHARACTERISTIC) on the characteristic
- *     variables (the paper's "primitive (or characteristic) variables");
+ *     variables (Sec. 2.2 allows either set to be reconstructed);
  *   - the HLLD Riemann flux (Miyoshi & Kusano 2005) on every x, y and z face,
  *     or HLL, or a learned per-face choice between the two;
  *   - the flux divergence of (rho, m, E);

@@ -5,11 +5,12 @@
  * and the CPU-baseline leg of the benchmark load it.  It shares no code with
  * the CUDA library: no header, helper or constant.
  *
- * What it computes (the gPLUTO method of the paper, Sec. 2.2: "reconstruction
- * of primitive variables, Riemann problem solution at cell interfaces, and
- * flux-conservative temporal update", with constrained transport for MHD;
- * the paper prints no formulas, so every step follows the published method it
- * names, written out below in the order the step performs it):
+ * What it computes (the gPLUTO method of the paper, Sec. 2.2, which names
+ * three stages -- reconstruct the primitives, solve a Riemann problem at every
+ * interface, update the conserved variables in flux form -- plus constrained
+ * transport for the field; the paper prints no formulas, so every step
+ * follows the published method it names, written out below in the order the
+ * step performs it):
  *
  *   state    5 cell-centred conserved variables (rho, mx, my, mz, E) and the
  *            three face-staggered normal field components (Bx at x-faces
