@@ -31,6 +31,10 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 PERIODIC, OUTFLOW = 0, 1
 HLLD, HLL, LEARNED, MASK = 0, 1, 2, 3
+# rounding thresholds of the branch decisions (HLLD degeneracy, mass-flux
+# deadband, characteristic degeneracies): those of the FP64 form, or those of
+# the FP32-bulk forms (mixed and FP32), which take the decisions in FP32
+THRESH_FP64, THRESH_FP32 = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -52,12 +56,17 @@ class _Cfg(C.Structure):
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("emf_mean", C.c_int), ("riemann", C.c_int),
                 ("mlp", C.POINTER(C.c_double)), ("mlp_zt", C.c_double),
-                ("choice", C.POINTER(C.c_ubyte)), ("recon", C.c_int)]
+                ("choice", C.POINTER(C.c_ubyte)), ("recon", C.c_int), ("thresholds", C.c_int)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("rho_floor_hits", C.c_longlong), ("p_floor_hits", C.c_longlong),
-                ("faces_hll", C.c_longlong), ("faces_hlld", C.c_longlong)]
+                ("faces_hll", C.c_longlong), ("faces_hlld", C.c_longlong),
+                ("hlld_region", C.c_longlong * 6), ("hlld_degenerate", C.c_longlong)]
+
+
+# HLLD regions, in the order of the region census (Stats.hlld_region)
+HLLD_REGIONS = ("L", "L*", "L**", "R**", "R*", "R")
 
 
 @dataclass
@@ -86,6 +95,8 @@ class Config:
     integrator: str = "rk2"
     # reconstruction: 0 = MC on the primitives, 1 = MC on the characteristic variables
     recon: int = 0
+    # THRESH_FP64 or THRESH_FP32: the branch thresholds of the form under test
+    thresholds: int = THRESH_FP64
 
     def c(self) -> _Cfg:
         mp = None
@@ -104,7 +115,7 @@ class Config:
             assert cp is not None, "MASK needs the per-face choices"
         return _Cfg(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.gamma, self.cfl,
                     (C.c_int * 3)(*self.bc), self.rho_floor, self.p_floor, self.emf_mean,
-                    self.riemann, mp, self.mlp_zt, cp, self.recon)
+                    self.riemann, mp, self.mlp_zt, cp, self.recon, self.thresholds)
 
     def face_shapes(self):
         o = [1 if b == OUTFLOW else 0 for b in self.bc]
@@ -137,6 +148,8 @@ def bind(L):
     L.orc_phys_flux.argtypes = [_P, C.c_double, C.c_double, _P]
     L.orc_hll.argtypes = [_P, _P, C.c_double, C.c_double, _P]
     L.orc_hlld.argtypes = [_P, _P, C.c_double, C.c_double, _P]
+    L.orc_hlld_region.restype = None
+    L.orc_hlld_region.argtypes = [_P, _P, C.c_double, C.c_double, _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     PP = _P * 5
     PF = _P * 3
     L.orc_step.restype = None
@@ -199,6 +212,16 @@ def hlld(wl, wr, bn: float, gamma: float) -> np.ndarray:
     return f
 
 
+def hlld_region(wl, wr, bn: float, gamma: float):
+    """(HLLD flux, name of the region it came from, number of star states
+    that took the degenerate branch)."""
+    wl, wr = _vec(wl, 7), _vec(wr, 7)
+    f = np.zeros(7)
+    reg, deg = C.c_int(-1), C.c_int(0)
+    lib().orc_hlld_region(_ptr(wl), _ptr(wr), bn, gamma, _ptr(f), C.byref(reg), C.byref(deg))
+    return f, HLLD_REGIONS[reg.value], deg.value
+
+
 def hll(wl, wr, bn: float, gamma: float) -> np.ndarray:
     wl, wr = _vec(wl, 7), _vec(wr, 7)
     f = np.zeros(7)
@@ -214,12 +237,18 @@ class Stats:
     p_floor_hits: int = 0
     faces_hll: int = 0
     faces_hlld: int = 0
+    # HLLD faces by region (keys HLLD_REGIONS) and degenerate star states
+    hlld_region: dict = field(default_factory=lambda: dict.fromkeys(HLLD_REGIONS, 0))
+    hlld_degenerate: int = 0
 
     def add(self, st):
         self.rho_floor_hits += st.rho_floor_hits
         self.p_floor_hits += st.p_floor_hits
         self.faces_hll += st.faces_hll
         self.faces_hlld += st.faces_hlld
+        for r, name in enumerate(HLLD_REGIONS):
+            self.hlld_region[name] += st.hlld_region[r]
+        self.hlld_degenerate += st.hlld_degenerate
 
 
 def _state_ptrs(cfg: Config, cell: np.ndarray, face):

@@ -70,14 +70,36 @@ typedef struct {
                                   cell s along d at [d * nx*ny*nz + s]; ghost faces take the
                                   choice of the cell they wrap to (periodic boxes) */
   int recon;        /* 0: MC on the primitives; 1: MC on the characteristic variables */
+  int thresholds;   /* rounding thresholds of the form under test: ORC_THRESH_FP64 (HLLD
+                       degeneracy 1e-12, mass-flux deadband 1e-10, characteristic degeneracies
+                       1e-12) or ORC_THRESH_FP32 (1e-6 for all three, the FP32-bulk forms) */
 } orc_cfg;
+
+#define ORC_THRESH_FP64 0
+#define ORC_THRESH_FP32 1
+
+static double degen_eps(const orc_cfg *c) { return c->thresholds == ORC_THRESH_FP32 ? 1e-6 : 1e-12; }
+static double band_eps(const orc_cfg *c) { return c->thresholds == ORC_THRESH_FP32 ? 1e-6 : 1e-10; }
 
 typedef struct {
   long long rho_floor_hits;
   long long p_floor_hits;
   long long faces_hll;    /* faces of interior cells solved with HLL ... */
   long long faces_hlld;   /* ... and with HLLD, per operator evaluation */
+  /* census of the HLLD faces of interior cells by the region whose flux they
+   * take: L, L*, L**, R**, R*, R (ORC_REG_*), and the number of star states
+   * (one per side of a face that reaches the star states) that took the
+   * degenerate branch */
+  long long hlld_region[6];
+  long long hlld_degenerate;
 } orc_stats;
+
+#define ORC_REG_L 0
+#define ORC_REG_LS 1
+#define ORC_REG_LSS 2
+#define ORC_REG_RSS 3
+#define ORC_REG_RS 4
+#define ORC_REG_R 5
 
 /* ------------------------------------------------------------------------ */
 /* single-face building blocks (exported so the tests can pin them alone)    */
@@ -159,12 +181,14 @@ void orc_hll(const double *wl, const double *wr, double bn, double gamma, double
  * (23), (43)-(48); outer Alfven speeds eq. (51); double-star states eqs.
  * (59)-(63); fluxes eqs. (64)-(66).  Readings where the paper is silent:
  *   - degenerate star state (den ~ 0): v*, B* keep the outer values when
- *     |den| <= 1e-12 max(|rho (S-u)(S-SM)|, bn^2);
+ *     |den| <= eps max(|rho (S-u)(S-SM)|, bn^2), eps = 1e-12 in FP64 (1e-6
+ *     for the FP32-bulk forms);
  *   - sign(0) = 0;
  *   - ties at exactly zero take the first listed region, scanning
  *     L, L*, L**, R**, R*, R. */
-void orc_hlld(const double *wl, const double *wr, double bn, double gamma, double *f) {
-  const double eps = 1e-12;
+static void hlld_flux(const double *wl, const double *wr, double bn, double gamma, double eps, double *f,
+                      int *region, int *ndegen) {
+  *ndegen = 0;
   double cl = orc_fast_speed(wl, bn, gamma), cr = orc_fast_speed(wr, bn, gamma);
   double cmax = cl > cr ? cl : cr;
   double sl = (wl[1] < wr[1] ? wl[1] : wr[1]) - cmax;
@@ -172,8 +196,8 @@ void orc_hlld(const double *wl, const double *wr, double bn, double gamma, doubl
   double fl[7], fr[7], ul[7], ur[7];
   orc_phys_flux(wl, bn, gamma, fl);
   orc_phys_flux(wr, bn, gamma, fr);
-  if (sl > 0.0) { memcpy(f, fl, 7 * sizeof(double)); return; }
-  if (sr < 0.0) { memcpy(f, fr, 7 * sizeof(double)); return; }
+  if (sl > 0.0) { memcpy(f, fl, 7 * sizeof(double)); *region = ORC_REG_L; return; }
+  if (sr < 0.0) { memcpy(f, fr, 7 * sizeof(double)); *region = ORC_REG_R; return; }
   w_to_u7(wl, bn, gamma, ul);
   w_to_u7(wr, bn, gamma, ur);
 
@@ -199,6 +223,7 @@ void orc_hlld(const double *wl, const double *wr, double bn, double gamma, doubl
     double vs, ws, bys, bzs;
     if (fabs(den) <= eps * scale) {
       vs = v; ws = ww; bys = by; bzs = bz;
+      ++*ndegen;
     } else {
       vs = v - bn * by * (sm - u) / den;
       ws = ww - bn * bz * (sm - u) / den;
@@ -225,10 +250,12 @@ void orc_hlld(const double *wl, const double *wr, double bn, double gamma, doubl
 
   if (ssl >= 0.0) {            /* left single-star region */
     for (int q = 0; q < 7; ++q) f[q] = fl[q] + sl * (us[0][q] - ul[q]);
+    *region = ORC_REG_LS;
     return;
   }
   if (sm < 0.0 && ssr < 0.0) { /* right single-star region */
     for (int q = 0; q < 7; ++q) f[q] = fr[q] + sr * (us[1][q] - ur[q]);
+    *region = ORC_REG_RS;
     return;
   }
   /* double-star states */
@@ -256,6 +283,19 @@ void orc_hlld(const double *wl, const double *wr, double bn, double gamma, doubl
   double so = a == 0 ? sl : sr, sso = a == 0 ? ssl : ssr;
   for (int q = 0; q < 7; ++q)
     f[q] = fo[q] + so * (us[a][q] - uu[q]) + sso * (uss[q] - us[a][q]);
+  *region = a == 0 ? ORC_REG_LSS : ORC_REG_RSS;
+}
+
+void orc_hlld(const double *wl, const double *wr, double bn, double gamma, double *f) {
+  int region, ndegen;
+  hlld_flux(wl, wr, bn, gamma, 1e-12, f, &region, &ndegen);
+}
+
+/* HLLD flux plus the region it came from (ORC_REG_*) and the number of star
+ * states that took the degenerate branch (0, 1 or 2). */
+void orc_hlld_region(const double *wl, const double *wr, double bn, double gamma, double *f,
+                     int *region, int *ndegen) {
+  hlld_flux(wl, wr, bn, gamma, 1e-12, f, region, ndegen);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -338,11 +378,12 @@ double orc_mlp_logit(const double *prm, const double *f) {
  * normalisation of Roe & Balsara (1996): with a^2 = gamma p / rho, the fast
  * and slow speeds c_f, c_s and the Alfven speed |bn|/sqrt(rho),
  *   alpha_f^2 = (a^2 - c_s^2)/(c_f^2 - c_s^2), alpha_s^2 = (c_f^2 - a^2)/(c_f^2 - c_s^2)
- *   (alpha_f = 1, alpha_s = 0 when c_f = c_s up to 1e-12),
- *   beta = B_t/|B_t| ((1, 1)/sqrt 2 when |B_t| vanishes up to 1e-12),
+ *   (alpha_f = 1, alpha_s = 0 when c_f = c_s up to eps),
+ *   beta = B_t/|B_t| ((1, 1)/sqrt 2 when |B_t| vanishes up to eps),
+ *   eps = 1e-12 in FP64 (1e-6 for the FP32-bulk forms),
  *   sgn(bn) = 1 for bn >= 0.
  * Waves in the order fast-, Alfven-, slow-, entropy, slow+, Alfven+, fast+. */
-void orc_char_eig(const double *w, double bn, double gamma, double *lam, double *R, double *L) {
+static void char_eig(const double *w, double bn, double gamma, double eps, double *lam, double *R, double *L) {
   double rho = w[0], u = w[1], p = w[4];
   double a2 = gamma * p / rho, a = sqrt(a2), sr = sqrt(rho);
   double bnr = bn / sr, b1 = w[5] / sr, b2 = w[6] / sr;
@@ -357,14 +398,14 @@ void orc_char_eig(const double *w, double bn, double gamma, double *lam, double 
   double cs2 = cf2 > 0.0 ? a2 * bnr * bnr / cf2 : 0.0;
   double cf = sqrt(cf2), cs = sqrt(cs2), ca = fabs(bnr);
   double bt = sqrt(bt2), be1, be2;
-  if (bt > 1e-12 * sqrt(a2 + bsq)) {
+  if (bt > eps * sqrt(a2 + bsq)) {
     be1 = b1 / bt;
     be2 = b2 / bt;
   } else {
     be1 = be2 = 1.0 / sqrt(2.0);
   }
   double af, as;
-  if (sq > 1e-12 * cf2) {
+  if (sq > eps * cf2) {
     double fa = 0.5 * (bsq - a2 + sq), as2 = 0.5 * (a2 - bsq + sq);   /* c_f^2 - a^2, a^2 - c_s^2 */
     af = sqrt((as2 > 0.0 ? as2 : 0.0) / sq);
     as = sqrt((fa > 0.0 ? fa : 0.0) / sq);
@@ -404,6 +445,10 @@ void orc_char_eig(const double *w, double bn, double gamma, double *lam, double 
 #undef LL
 }
 
+void orc_char_eig(const double *w, double bn, double gamma, double *lam, double *R, double *L) {
+  char_eig(w, bn, gamma, 1e-12, lam, R, L);
+}
+
 /* MC limiter of a difference pair: sign(dp) min(2|dm|, 2|dp|, |dm+dp|/2)
  * when dm dp > 0, else 0 (orc_mc_slope on the differences). */
 static double mc_lim(double dm, double dp) {
@@ -418,9 +463,10 @@ static double mc_lim(double dm, double dp) {
  * primitives: the differences projected on the left eigenvectors of the
  * middle cell, limited wave by wave, projected back with its right
  * eigenvectors.  bn0: the middle cell's cell-centred normal field. */
-void orc_char_slope(const double *wm, const double *w0, const double *wp, double bn0, double gamma, double *slope) {
+static void char_slope(const double *wm, const double *w0, const double *wp, double bn0, double gamma, double eps,
+                       double *slope) {
   double lam[7], R[49], L[49], dm[7], dp[7], cm[7], cp[7], dc[7];
-  orc_char_eig(w0, bn0, gamma, lam, R, L);
+  char_eig(w0, bn0, gamma, eps, lam, R, L);
   for (int v = 0; v < 7; ++v) {
     dm[v] = w0[v] - wm[v];
     dp[v] = wp[v] - w0[v];
@@ -437,6 +483,10 @@ void orc_char_slope(const double *wm, const double *w0, const double *wp, double
     slope[v] = 0.0;
     for (int k = 0; k < 7; ++k) slope[v] += R[v * 7 + k] * dc[k];
   }
+}
+
+void orc_char_slope(const double *wm, const double *w0, const double *wp, double bn0, double gamma, double *slope) {
+  char_slope(wm, w0, wp, bn0, gamma, 1e-12, slope);
 }
 
 typedef struct {
@@ -578,7 +628,8 @@ static void rotated(const grid *g, double *W[8], int d, size_t q, double *w) {
  * extended grid.  F[q] (q = 0..6, rotated order) is stored at the (N+1)^3
  * lattice index of the face's right cell (face I = left face of cell I).
  * M holds the mass flux that orients the upwind EMF average: F[0] itself,
- * or exactly 0 when |F[0]| <= 1e-10 (rho_L + rho_R)/2 max(c_fL, c_fR), so a
+ * or exactly 0 when |F[0]| <= eps (rho_L + rho_R)/2 max(c_fL, c_fR) (eps =
+ * 1e-10 in FP64, 1e-6 for the FP32-bulk forms), so a
  * mass flux that vanishes up to rounding takes the mean of both sides
  * (reading of the tie rule, which the method leaves open). */
 static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7], double *M) {
@@ -602,8 +653,8 @@ static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7
         double sL[7], sR[7], wl[7], wr[7];
         if (c->recon == 1) {
           /* characteristic slopes with each cell's own cell-centred normal field */
-          orc_char_slope(wm2, wm1, w0, W[5 + d][q0 - st], c->gamma, sL);
-          orc_char_slope(wm1, w0, wp1, W[5 + d][q0], c->gamma, sR);
+          char_slope(wm2, wm1, w0, W[5 + d][q0 - st], c->gamma, degen_eps(c), sL);
+          char_slope(wm1, w0, wp1, W[5 + d][q0], c->gamma, degen_eps(c), sR);
         } else {
           for (int v = 0; v < 7; ++v) {
             sL[v] = orc_mc_slope(wm2[v], wm1[v], w0[v]);
@@ -642,16 +693,22 @@ static void sweep(const grid *g, double *W[8], double *Bf[3], int d, double *F[7
           use_hlld = c->choice[(size_t)d * nint + s_own] != 0;
         }
         double f[7];
-        if (use_hlld) orc_hlld(wl, wr, bn, c->gamma, f);
+        int region = 0, ndegen = 0;
+        if (use_hlld) hlld_flux(wl, wr, bn, c->gamma, degen_eps(c), f, &region, &ndegen);
         else orc_hll(wl, wr, bn, c->gamma, f);
         if (interior && g->st) {
-          if (use_hlld) g->st->faces_hlld++;
-          else g->st->faces_hll++;
+          if (use_hlld) {
+            g->st->faces_hlld++;
+            g->st->hlld_region[region]++;
+            g->st->hlld_degenerate += ndegen;
+          } else {
+            g->st->faces_hll++;
+          }
         }
         size_t fq = fidx(g, I, J, K);
         for (int v = 0; v < 7; ++v) F[v][fq] = f[v];
         double cl = orc_fast_speed(wl, bn, c->gamma), cr = orc_fast_speed(wr, bn, c->gamma);
-        double band = 1e-10 * 0.5 * (wl[0] + wr[0]) * (cl > cr ? cl : cr);
+        double band = band_eps(c) * 0.5 * (wl[0] + wr[0]) * (cl > cr ? cl : cr);
         M[fq] = fabs(f[0]) <= band ? 0.0 : f[0];
       }
 }
