@@ -32,12 +32,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-updates/s on 1 GB300 at 256^3 MHD; % HBM roofline; vs plain FP64 at L1 error"
 UNIT = "Mcell-updates/s"
-# algorithmic HBM bytes per cell per stage-kernel launch: stage 1 reads the
-# primitives W (11 arrays) and U^n (8), writes K1 (8) and W(U*); stage 2 reads
-# W(U*), U^n and K1, writes U^{n+1} and W(U^{n+1})
+# Minimum algorithmic HBM bytes per cell per stage launch (the roofline's
+# numerator): only the conserved states move, halos come from cache.  RK2:
+# stage 1 reads U^n (8 values) and writes U*, stage 2 reads U* and U^n and
+# writes U^{n+1}; U^n and U^{n+1} are FP64 in the FP64 and mixed forms, U*
+# is FP64 / FP32 / FP32.  FP64 128 + 192 = 320 B per cell-update, mixed
+# 96 + 160 = 256, FP32 64 + 96 = 160.
+MIN_STAGE_BYTES = {"fp64": (128, 192), "mixed": (96, 160), "fp32": (64, 96)}
+# SSP-RK3 the same way: U1 and U2 in the bulk precision, U^n re-read by stages 2 and 3
+MIN_STAGE_BYTES_RK3 = {"fp64": (128, 192, 192), "mixed": (96, 128, 160), "fp32": (64, 96, 96)}
+# What this design's stage kernels move (reported beside the minimum): the
+# primitives W (11 arrays) are stored once per state instead of recomputed in
+# every halo copy, and RK2's stage increment K1 is stored in the bulk
+# precision.  Stage 1 reads W and U^n, writes K1 and W(U*); stage 2 reads
+# W(U*), U^n and K1, writes U^{n+1} and W(U^{n+1}).
 STAGE_BYTES = {"fp64": (304, 368), "mixed": (184, 248), "fp32": (152, 184)}
 # SSP-RK3 stages: read W(U_in), U_in (and U^n in stages 2, 3), write U_out, W(U_out)
 STAGE_BYTES_RK3 = {"fp64": (304, 368, 368), "mixed": (216, 280, 280), "fp32": (152, 184, 184)}
+# the host-core oracle legs (cpu_baseline and --impl reference) step one
+# sample box of this edge per process
+CPU_SAMPLE_N = 64
 # the paper's own run of this workload (FP64, RK3, 3D OT 352^3, 10 steps): context, not a target
 PAPER_OT352 = {"time_10_steps_s": 13.9, "hardware": "NVIDIA A100 64 GB (Leonardo), NVHPC 24.5 OpenACC, managed memory",
                "note": "total time of 10 steps of the paper's 3D Orszag-Tang test (Sec. 4, its figure of total "
@@ -300,23 +314,64 @@ def traffic_from_profiles(kernel_tag):
     return (float(rec["dram_bytes_per_launch"]) if rec else None), digest
 
 
-def cpu_oracle_rate(seconds: float, n: int = 64):
-    """Time the FP64 oracle (as it stands, one host thread) on an n^3 sample
-    of the turbulence workload until ``seconds`` of CPU work have run."""
+def _oracle_worker(n, warmup, steps, barrier, seconds=None):
+    """One host process: the FP64 oracle (as it stands) on its own n^3 sample
+    of the turbulence workload; `warmup` untimed steps, then `steps` timed
+    steps (or as many as fit in `seconds`).  Returns (cells x steps, seconds)."""
     import oracle as O
     from paper_2606_12753_gb300 import inputs as I
     box = I.turbulence_3d(n)
     cfg = O.Config(box.nx, box.ny, box.nz, box.dx, box.dy, box.dz, box.gamma, 0.4, box.bc)
     cell, face = box.cell, box.face
-    steps, t0 = 0, time.perf_counter()
-    while True:
+    for _ in range(warmup):
         cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or steps >= 1000:
-            break
-    return {"value": box.ncell * steps / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"turbulence_3d recipe at {n}^3, {steps} RK2 steps with CFL dt, single host thread, {el:.1f} s"}
+    if barrier is not None:
+        barrier.wait()
+    done, t0 = 0, time.perf_counter()
+    while done < steps or (seconds is not None and time.perf_counter() - t0 < seconds):
+        cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
+        done += 1
+    return box.ncell * done, time.perf_counter() - t0
+
+
+def oracle_throughput(n: int, steps: int, warmup: int, workers: int, seconds=None):
+    """Whole-host rate of the oracle: `workers` independent processes (spawned,
+    so none inherits a CUDA context), each stepping its own sample, released
+    together after their warm-up.  Rate = all cell-updates / the slowest
+    process's time.  Returns (Mcell-updates/s, cell-updates, seconds)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle as O
+    O.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(workers) if workers > 1 else None
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+            futs = [ex.submit(_oracle_worker, n, warmup, steps, barrier, seconds) for _ in range(workers)]
+            res = [f.result() for f in futs]
+    cells = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return cells / el / 1e6, cells, el
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(seconds: float, n: int = CPU_SAMPLE_N):
+    """The FP64 oracle on the host cores: one process per core, each on its
+    own n^3 sample of the turbulence workload, for about ``seconds``; plus the
+    same on one core alone."""
+    cores = host_cores()
+    one, _, el1 = oracle_throughput(n, 0, 0, 1, seconds=seconds / 3)
+    allc, cells, el = oracle_throughput(n, 1, 0, cores, seconds=seconds)
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"turbulence_3d recipe at {n}^3 per process, {cores} processes (one per host core) of "
+                      f"RK2 steps with CFL dt for {el:.1f} s ({cells / n ** 3:.0f} box-steps)",
+            "single_core": {"value": one, "cores": 1, "seconds": round(el1, 1)}}
 
 
 WORKLOADS = {
@@ -375,26 +430,17 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle as O
-    from paper_2606_12753_gb300 import inputs as I
-    O.build()
-    n = 48
-    box = I.turbulence_3d(n)
-    cfg = O.Config(box.nx, box.ny, box.nz, box.dx, box.dy, box.dz, box.gamma, 0.4, box.bc)
-    cell, face = box.cell, box.face
-    for _ in range(args.warmup):
-        cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        cell, face, _ = O.step(cfg, cell, face, -1.0, nsteps=1)
-    el = time.perf_counter() - t0
-    value = box.ncell * args.steps / el / 1e6
-    sample = f"turbulence_3d recipe at {n}^3 (each step one RK2 step of the FP64 oracle, one host thread)"
+    n = CPU_SAMPLE_N
+    cores = host_cores()
+    value, cells, el = oracle_throughput(n, args.steps, args.warmup, cores)
+    sample = (f"turbulence_3d recipe at {n}^3 per process, {cores} processes (one per host core); each step is "
+              f"one RK2 step of the FP64 oracle in every process")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": dict(workload_config(args), sample=f"{n}^3 per step, FP64 oracle"),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "data": "synthetic",
+           "config": dict(workload_config(args), sample=f"{cores} x {n}^3 per step, FP64 oracle on the host cores"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
     print(json.dumps(out), flush=True)
@@ -416,6 +462,7 @@ def run_ours(args):
     learned = args.workload == "turbulence256_learned"
     rk3 = args.workload == "ot3d352_rk3"
     stage_bytes = (STAGE_BYTES_RK3 if rk3 else STAGE_BYTES)[args.precision]
+    min_bytes = (MIN_STAGE_BYTES_RK3 if rk3 else MIN_STAGE_BYTES)[args.precision]
     switch_rep = None
     if learned:
         # training (not timed): faces of FP64 turbulence runs with seed 5,
@@ -479,8 +526,9 @@ def run_ours(args):
     nst = len(stage_bytes)
     k = max(range(nst), key=lambda i: stage_ms[i] / max(launches[i], 1))
     per_launch_ms = stage_ms[k] / max(launches[k], 1)
-    alg_bytes = stage_bytes[k] * box.ncell
+    alg_bytes = min_bytes[k] * box.ncell
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    design_achieved = stage_bytes[k] * box.ncell / (per_launch_ms / 1e3) / 1e9
     kname = "stage_kernel" + ("_learned" if learned else "") + ("_rk3" if rk3 else "") + \
         ("_char" if args.recon == "characteristic" else "")
     tag = f"{kname}<{args.precision},{k + 1}>@{box.name}"
@@ -501,7 +549,10 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": tag, "peak_kind": peak_kind,
-                     "step_frac": value * 1e6 / world * sum(stage_bytes) / 1e9 / peak},
+                     "bytes_per_cell": min_bytes[k], "bytes_basis": "minimum: conserved states only",
+                     "traffic_ratio": traffic / alg_bytes if traffic else None,
+                     "frac_design": design_achieved / peak, "design_bytes_per_cell": stage_bytes[k],
+                     "step_frac": value * 1e6 / world * sum(min_bytes) / 1e9 / peak},
         "stage_ms_per_launch": [stage_ms[i] / max(launches[i], 1) for i in range(nst)],
         "gpu_launches": nst * args.steps,
     }
@@ -685,8 +736,13 @@ def run_batch(args):
     batch = mhd.Batch(boxes, precision=args.precision, stream=stream.cuda_stream)
     for i, b in enumerate(boxes):
         batch.set_state(i, b.cell, b.face)
-    cache = os.environ.get("MHD_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "mhd_autotune.jsonl")
-    tile, tune_ms = batch.autotune(trial_steps=3, cache_path=cache)
+    tile = tuple(int(x) for x in args.tile.split(","))
+    if any(tile):
+        batch.set_tile(*tile)       # an explicit tile: no autotuning (a fixed launch sequence)
+        tune_ms = None
+    else:
+        cache = os.environ.get("MHD_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "mhd_autotune.jsonl")
+        tile, tune_ms = batch.autotune(trial_steps=3, cache_path=cache)
     def timed_once():
         clk = ClockSampler(local).start()
         batch.step(-1.0, args.warmup)
@@ -715,9 +771,13 @@ def run_batch(args):
         raise RuntimeError(f"device status {st['status']} after the timed steps")
     value = job_rate(ncell, args.steps, ms_total, world)
     peak, peak_kind = peaks()
-    step_bytes = sum(STAGE_BYTES[args.precision]) * ncell
+    step_bytes = sum(MIN_STAGE_BYTES[args.precision]) * ncell
     achieved = step_bytes * args.steps / (ms_total / 1e3) / 1e9
+    design_achieved = sum(STAGE_BYTES[args.precision]) * ncell * args.steps / (ms_total / 1e3) / 1e9
     (tx, ty, tz), items, grid = batch.tile()
+    seq = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        seq = single_box_sequence(args, boxes, stream, barrier)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -729,16 +789,74 @@ def run_batch(args):
                    "parallelism": (f"replicas x{world}, " if world > 1 else "") + "all boxes of a GPU in one launch"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": f"batch_kernel<{args.precision},{tx}x{ty}>@blast_batch_{args.n}",
-                     "peak_kind": peak_kind},
+                     "peak_kind": peak_kind, "bytes_per_cell": sum(MIN_STAGE_BYTES[args.precision]),
+                     "bytes_basis": "minimum: conserved states only, per cell-update",
+                     "frac_design": design_achieved / peak},
         "gpu_launches": 2 if args.steps else 0,
         "e2e": None,
         "clocks": clocks,
     }
+    if seq is not None:
+        out["vs_single_box_calls"] = {**seq, "batched_value": value, "batched_over_single": value / seq["value"]}
     batch.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def single_box_sequence(args, boxes, stream, barrier):
+    """The same boxes advanced through one single-box handle each (the plain
+    path): per step, every handle's RK2 step with its own CFL dt (2 stage
+    launches per box), all K steps captured in one CUDA graph and replayed,
+    timed like the batch.  Returns the rate and how it was taken."""
+    import torch
+    from paper_2606_12753_gb300 import mhd
+    solvers = [mhd.Solver(b, precision=args.precision, stream=stream.cuda_stream) for b in boxes]
+    for s, b in zip(solvers, boxes):
+        s.set_state(b.cell, b.face)
+    for s in solvers:
+        s.step_async(-1.0, 2)          # primitives valid, every handle warm
+    torch.cuda.synchronize()
+    k = args.steps + (args.steps % 2)  # an even count returns each ping-pong buffer to its start
+    graph, mode = None, "CUDA graph of K steps x 64 handles"
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(k):
+                for s in solvers:
+                    s.step_async(-1.0, 1)
+    except Exception as exc:                                 # capture refused: time plain launches
+        graph, mode = None, f"asynchronous launches (graph capture failed: {type(exc).__name__})"
+        torch.cuda.synchronize()
+
+    def run():
+        if graph is not None:
+            with torch.cuda.stream(stream):   # replay on the stream the events are recorded on
+                graph.replay()
+        else:
+            for _ in range(k):
+                for s in solvers:
+                    s.step_async(-1.0, 1)
+
+    for _ in range(max(1, args.warmup // 2)):
+        run()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run()
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    bad = [s.stats()["status"] for s in solvers if s.stats()["status"] != 0]
+    for s in solvers:
+        s.close()
+    if bad:
+        raise RuntimeError(f"device status {bad[0]} in the single-box sequence")
+    ncell = sum(b.ncell for b in boxes)
+    return {"value": ncell * k / (ms / 1e3) / 1e6, "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+            "launches_per_step": 2 * len(boxes), "mode": mode}
 
 
 def main():

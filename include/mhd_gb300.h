@@ -60,6 +60,7 @@ extern "C" {
 #define MHD_ERR_NONFINITE (-3) /* a NaN or Inf state value was met on the device */
 #define MHD_ERR_TIMEOUT (-4)   /* a device-wide barrier gave up waiting */
 #define MHD_ERR_NOMEM (-5)     /* device allocation failed */
+#define MHD_ERR_FLOOR (-6)     /* a density or pressure floor was applied (only with MHD_FLOOR_ERROR) */
 
 #define MHD_BC_PERIODIC 0
 #define MHD_BC_OUTFLOW 1
@@ -85,6 +86,10 @@ extern "C" {
 #define MHD_EMF_UPWIND 0 /* Gardiner & Stone (2005) upwind contact average */
 #define MHD_EMF_MEAN 1   /* arithmetic mean of the four face EMFs (debug) */
 
+#define MHD_FLOOR_COUNT 0 /* floors are applied and counted (mhd_get_stats); calls succeed (default) */
+#define MHD_FLOOR_ERROR 1 /* as COUNT, and a synchronising single-box call returns MHD_ERR_FLOOR when the
+                             floor counters rose since the previous synchronising call */
+
 typedef struct {
   int nx, ny, nz;          /* cells per axis (>= 1; >= 2 on an outflow axis) */
   double dx, dy, dz;       /* cell sizes */
@@ -99,10 +104,12 @@ typedef struct {
   int tile_x, tile_y, tile_z; /* tile of the fused stage kernel; 0 = default */
   int integrator;          /* MHD_RK2 | MHD_RK3 */
   int recon;               /* MHD_RECON_PRIMITIVE | MHD_RECON_CHARACTERISTIC */
+  int floor_policy;        /* MHD_FLOOR_COUNT | MHD_FLOOR_ERROR */
 } mhd_config;
 
 typedef struct {
-  long long rho_floor_hits; /* cell-stage evaluations that hit the density floor */
+  long long rho_floor_hits; /* primitive recoveries that hit the density floor: one per cell for a state
+                               set from outside, then one per cell and stage */
   long long p_floor_hits;   /* ... the pressure floor */
   long long faces_hll;      /* MHD_LEARNED only: face solves (halo faces of neighbouring tiles
                                recomputed included) that took HLL ... */
@@ -114,28 +121,45 @@ typedef struct {
 
 typedef struct mhd_handle mhd_handle;
 
-/* Fill *cfg with defaults for an n = (nx, ny, nz) periodic box on [0,1]^3. */
+/* Fill *cfg with defaults for an n = (nx, ny, nz) periodic box on [0,1]^3:
+ * gamma 5/3, Courant number 0.4, FP64, HLLD, upwind EMFs, floors 1e-10,
+ * default tile, RK2, primitive reconstruction, floors counted. */
 void mhd_default_config(mhd_config* cfg, int nx, int ny, int nz);
 
 /* Validate cfg, allocate the handle's device buffers (state, stage buffer,
  * status words) and bind it to `cuda_stream` (a cudaStream_t, or NULL).
+ * The handle holds one box of the uniform Cartesian grid on which the paper's
+ * per-step update runs (Sec. 2.2: the state of the conserved variables, with
+ * the field kept on the cell faces for constrained transport).  cfg is read
+ * during the call only; the handle belongs to the caller until mhd_destroy.
  * Returns MHD_ERR_INVALID for a bad configuration, MHD_ERR_NOMEM when the
  * device allocation fails.  *out is set only on success. */
 int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle** out);
 
-/* Copy a state in.  cell[0..4] = rho, mx, my, mz, E; face[0..2] = Bx, By, Bz
- * in the layout above.  on_device = 1: the pointers are device addresses on
- * the handle's device; 0: host addresses (pageable or pinned). */
+/* Copy a state in: the conserved variables the step advances (Sec. 2.2),
+ * cell[0..4] = rho, mx, my, mz, E; face[0..2] = Bx, By, Bz in the layout
+ * above.  on_device = 1: the pointers are device addresses on the handle's
+ * device; 0: host addresses (pageable or pinned).  The arrays are copied; the
+ * caller keeps them.  Errors: MHD_ERR_INVALID (null pointer), MHD_ERR_CUDA. */
 int mhd_set_state(mhd_handle* h, const void* const cell[5], const void* const face[3], int on_device);
 
-/* Copy the current state out (same layout and pointer kinds); synchronises. */
+/* Copy the current state out (same layout and pointer kinds, caller-owned
+ * arrays, the state of Sec. 2.2's update); synchronises.  Errors as
+ * mhd_set_state. */
 int mhd_get_state(mhd_handle* h, void* cell[5], void* face[3], int on_device);
 
-/* Advance nsteps steps of the configured integrator (RK2 or SSP-RK3).
- * dt > 0: that dt for every step.  dt <= 0: each step takes the CFL dt of its
- * own starting state, reduced on the device (no host round trip).  Enqueues 2
- * (RK2) or 3 (RK3) kernels per step; synchronises once at the end to read
- * the status word. */
+/* Advance nsteps steps of the configured integrator (RK2 or SSP-RK3): the
+ * paper's per-step update (Sec. 2.2: reconstruction, a Riemann solve per
+ * interface, the flux-conservative update, constrained transport of the face
+ * field, inside the stages of a Runge-Kutta step; Table 2's Reconstruct,
+ * HLLD_Solver, RightHandSide, CT_EMF and US kernels fused into one launch per
+ * stage).  dt > 0: that dt for every step.  dt <= 0: each step takes the CFL
+ * dt of its own starting state, reduced on the device (no host round trip).
+ * Enqueues 2 (RK2) or 3 (RK3) kernels per step; synchronises once at the end
+ * to read the status word.  Errors: MHD_ERR_INVALID (nsteps < 0, NaN dt),
+ * MHD_ERR_CUDA, MHD_ERR_NONFINITE (a non-finite value met on the device; the
+ * state is then undefined), MHD_ERR_FLOOR (MHD_FLOOR_ERROR only; the step was
+ * taken). */
 int mhd_step(mhd_handle* h, double dt, int nsteps);
 
 /* ---- host streaming -------------------------------------------------------
@@ -183,13 +207,19 @@ int mhd_get_profile(mhd_handle* h, double ms[3], long long launches[3]);
  * and MHD_FP32.  The state is unchanged; synchronises. */
 int mhd_rhs(mhd_handle* h, void* cell[5], void* face[3], int on_device);
 
-/* CFL dt of the current state (FP64 reduction on the device); synchronises. */
+/* CFL dt of the current state (FP64 reduction on the device; the time step of
+ * the Runge-Kutta driver, Sec. 2.2, from the largest signal speed over the
+ * cells); synchronises.  *dt_out is caller-owned.  Errors: MHD_ERR_INVALID
+ * (null pointer), MHD_ERR_CUDA. */
 int mhd_cfl_dt(mhd_handle* h, double* dt_out);
 
-/* max over cells of |div B| = |sum_d (B_d(i_d+1) - B_d(i_d)) / Delta_d|, FP64. */
+/* max over cells of |div B| = |sum_d (B_d(i_d+1) - B_d(i_d)) / Delta_d|, FP64:
+ * the constraint that constrained transport (Sec. 2.2) keeps at rounding
+ * level.  Synchronises; errors as mhd_cfl_dt. */
 int mhd_divb_max(mhd_handle* h, double* out);
 
-/* One RK2 step of one box that allocates no device memory, for callers that
+/* One RK2 step of one box, HLLD or HLL, primitive reconstruction, that
+ * allocates no device memory, for callers that
  * must not call cudaMalloc while they run (a service that reserves its device
  * memory up front and must not allocate later, a framework whose own pool
  * accounts for every device byte, a loop that cannot take the device-wide
@@ -206,12 +236,14 @@ int mhd_divb_max(mhd_handle* h, double* out);
  * until it is unloaded.  A box needs 2*ceil256(8*T*e) + ceil256(8*T*k) +
  * 2*ceil256(11*N*k) + 512 bytes of it (N cells, T = total state elements, e =
  * 8 or 4 bytes per state element, k = 8 or 4 per increment / primitive); at
- * 8 MiB that is up to about 20k cells in FP64 and 40k in FP32 (for example
- * 24^3 in FP64, 32^3 in FP32).  Larger boxes are rejected with
- * MHD_ERR_INVALID.  The first call on a device resolves the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture on the device.  All calls share the array: calls whose work
- * overlaps on the GPU race and must be serialised by the caller.
+ * 8 MiB that is up to about 20k cells in FP64, 33k in the mixed form and 40k
+ * in FP32 (for example 24^3 in FP64, 30^3 mixed, 32^3 in FP32).  Larger boxes
+ * are rejected with MHD_ERR_INVALID.  The first call on a device resolves the
+ * array's device address (cudaGetSymbolAddress).  Every call ends by
+ * synchronising its stream (it reads the status word back), so it cannot be
+ * issued while that stream is being captured into a CUDA graph.  All calls
+ * share the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  The error text is kept per host thread.
  * Errors: MHD_ERR_INVALID (bad config, null pointer, box too large),
  * MHD_ERR_CUDA, MHD_ERR_NONFINITE; the text is in mhd_last_error(NULL). */
 #define MHD_NOALLOC_SCRATCH_BYTES (8u << 20)
@@ -219,7 +251,9 @@ int mhd_step_noalloc(const mhd_config* cfg, void* cuda_stream, const void* const
                      const void* const face_in[3], void* cell_out[5], void* face_out[3], double dt,
                      double* dt_used);
 
-/* Counters and the device status word; synchronises. */
+/* Counters and the device status word (floor hits of the primitive
+ * recovery of Sec. 2.2's reconstruction step, HLL/HLLD face counts of the
+ * learned switch); synchronises.  Does not itself return MHD_ERR_FLOOR. */
 int mhd_get_stats(mhd_handle* h, mhd_stats* out);
 
 /* ------------------------------------------------------------------------
@@ -347,11 +381,16 @@ typedef struct {
 } mhd_pipe_peaks;
 int mhd_measure_pipe_peaks(void* cuda_stream, mhd_pipe_peaks* out);
 
-/* Free every resource of the handle (NULL is a no-op). */
+/* Free every resource of the handle: the box's state, the stage buffers of
+ * the Runge-Kutta step (Sec. 2.2) and its status words.  Synchronises the
+ * handle's stream first, so no enqueued work still uses them.  NULL is a
+ * no-op; the handle must not be used afterwards. */
 void mhd_destroy(mhd_handle* h);
 
-/* Text of the last failure on h (or of the last failed mhd_create when h is
- * NULL).  The string lives until the next call on h. */
+/* Text of the last failure on h (or, when h is NULL, of the calling host
+ * thread's last failed call that has no handle: mhd_create, mhd_step_noalloc,
+ * mhd_measure_pipe_peaks).  The string lives until the next call on h (on
+ * that thread). */
 const char* mhd_last_error(const mhd_handle* h);
 
 #ifdef __cplusplus

@@ -56,7 +56,8 @@ class _Cfg(C.Structure):
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("emf_mean", C.c_int), ("riemann", C.c_int),
                 ("mlp", C.POINTER(C.c_double)), ("mlp_zt", C.c_double),
-                ("choice", C.POINTER(C.c_ubyte)), ("recon", C.c_int), ("thresholds", C.c_int)]
+                ("choice", C.POINTER(C.c_ubyte)), ("recon", C.c_int), ("thresholds", C.c_int),
+                ("thresh_scale", C.c_double)]
 
 
 class _Stats(C.Structure):
@@ -97,6 +98,8 @@ class Config:
     recon: int = 0
     # THRESH_FP64 or THRESH_FP32: the branch thresholds of the form under test
     thresholds: int = THRESH_FP64
+    # every branch threshold times this factor (sensitivity of the decisions)
+    thresh_scale: float = 1.0
 
     def c(self) -> _Cfg:
         mp = None
@@ -115,7 +118,7 @@ class Config:
             assert cp is not None, "MASK needs the per-face choices"
         return _Cfg(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.gamma, self.cfl,
                     (C.c_int * 3)(*self.bc), self.rho_floor, self.p_floor, self.emf_mean,
-                    self.riemann, mp, self.mlp_zt, cp, self.recon, self.thresholds)
+                    self.riemann, mp, self.mlp_zt, cp, self.recon, self.thresholds, self.thresh_scale)
 
     def face_shapes(self):
         o = [1 if b == OUTFLOW else 0 for b in self.bc]

@@ -73,13 +73,16 @@ typedef struct {
   int thresholds;   /* rounding thresholds of the form under test: ORC_THRESH_FP64 (HLLD
                        degeneracy 1e-12, mass-flux deadband 1e-10, characteristic degeneracies
                        1e-12) or ORC_THRESH_FP32 (1e-6 for all three, the FP32-bulk forms) */
+  double thresh_scale; /* sensitivity of those decisions: every threshold times this factor
+                          (0 is read as 1) */
 } orc_cfg;
 
 #define ORC_THRESH_FP64 0
 #define ORC_THRESH_FP32 1
 
-static double degen_eps(const orc_cfg *c) { return c->thresholds == ORC_THRESH_FP32 ? 1e-6 : 1e-12; }
-static double band_eps(const orc_cfg *c) { return c->thresholds == ORC_THRESH_FP32 ? 1e-6 : 1e-10; }
+static double thresh_factor(const orc_cfg *c) { return c->thresh_scale > 0.0 ? c->thresh_scale : 1.0; }
+static double degen_eps(const orc_cfg *c) { return (c->thresholds == ORC_THRESH_FP32 ? 1e-6 : 1e-12) * thresh_factor(c); }
+static double band_eps(const orc_cfg *c) { return (c->thresholds == ORC_THRESH_FP32 ? 1e-6 : 1e-10) * thresh_factor(c); }
 
 typedef struct {
   long long rho_floor_hits;

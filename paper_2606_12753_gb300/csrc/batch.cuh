@@ -1,9 +1,11 @@
 // Batched persistent launch: many independent boxes of uneven size advance
 // in ONE cooperative kernel.  Work items are (box, tile, z-chunk) of the fused
-// stage kernel; the CTAs of a persistent grid (all co-resident) take items in
-// a strided order, meet at a device-wide barrier after each RK stage, and go
-// on to the next stage / step.  Every box keeps its own CFL dt (the max that
-// its stage 2 folded into the box's own word).  The barrier gives up after a
+// stage kernel, listed by the host longest first (a chunk's cost grows with
+// its planes plus the three-plane prologue of its march); the CTAs of a
+// persistent grid (all co-resident) draw the next item of the list from a
+// device counter as they finish one, meet at a device-wide barrier after each
+// RK stage, and go on to the next stage / step.  Every box keeps its own CFL
+// dt (the max that its stage 2 folded into the box's own word).  The barrier gives up after a
 // %globaltimer limit, raises the timeout bit of the status word and every CTA
 // returns, so the host sees MHD_ERR_TIMEOUT and the context stays usable.
 #pragma once
@@ -23,9 +25,17 @@ struct BoxDesc {
   int parity;                  // words[parity] holds its CFL max
 };
 
+// one entry of the item list: box, and the item's index within the box
+struct ItemRef {
+  int box;
+  int local;
+};
+
 struct BatchArgs {
   BoxDesc* boxes;
   int nbox;
+  const ItemRef* order;        // the items, longest first
+  unsigned long long* work;    // draws from the item list, monotone over one launch (zeroed before it)
   long long total_items;
   int nsteps;
   double dt;                   // > 0: every box takes this dt; <= 0: its own CFL dt
@@ -71,15 +81,6 @@ __device__ __forceinline__ bool grid_barrier(const BatchArgs& ba, unsigned epoch
   return ok != 0;
 }
 
-__device__ __forceinline__ int find_box(const BatchArgs& ba, long long item) {
-  int lo = 0, hi = ba.nbox - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ba.boxes[mid].item_begin <= item) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 __device__ __forceinline__ StageArgs box_stage_args(const BatchArgs& ba, const BoxDesc& bd, int stage, int step) {
   StageArgs a;
   const int cur = (bd.cur + step) & 1;
@@ -98,20 +99,31 @@ __device__ __forceinline__ StageArgs box_stage_args(const BatchArgs& ba, const B
   return a;
 }
 
+// Every CTA draws items until the list of the stage is exhausted: each draw
+// takes the next ticket of the launch's counter, and each CTA makes exactly
+// one draw past the end per stage, so stage e (0-based within the launch)
+// owns tickets [e (T + G), (e + 1)(T + G)) for T items and G CTAs, and no
+// draw of stage e + 1 starts before the barrier that ends stage e.
 template <int PREC, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 3) batch_kernel(BatchArgs ba) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long next_item;
+  const unsigned long long per_stage = (unsigned long long)ba.total_items + gridDim.x;
   unsigned epoch = 0;
   for (int step = 0; step < ba.nsteps; ++step) {
 #pragma unroll 1
     for (int stage = 1; stage <= 2; ++stage) {
-      for (long long it = blockIdx.x; it < ba.total_items; it += gridDim.x) {
-        const int box = find_box(ba, it);
-        const BoxDesc& bd = ba.boxes[box];
+      const unsigned long long base = (unsigned long long)epoch * per_stage;
+      for (;;) {
+        if (threadIdx.x == 0) next_item = (long long)(atomicAdd(ba.work, 1ull) - base);
+        __syncthreads();
+        const long long it = next_item;   // every thread reads it before run_item's first barrier
+        if (it >= ba.total_items) break;
+        const ItemRef ref = ba.order[it];
+        const BoxDesc& bd = ba.boxes[ref.box];
         const StageArgs a = box_stage_args(ba, bd, stage, step);
-        const int local = (int)(it - bd.item_begin);
-        if (stage == 1) StageKernel<PREC, 1, TX, TY>::run_item(bd.g, a, local, smem_raw);
-        else StageKernel<PREC, 2, TX, TY>::run_item(bd.g, a, local, smem_raw);
+        if (stage == 1) StageKernel<PREC, 1, TX, TY>::run_item(bd.g, a, ref.local, smem_raw);
+        else StageKernel<PREC, 2, TX, TY>::run_item(bd.g, a, ref.local, smem_raw);
       }
       if (!grid_barrier(ba, ++epoch)) return;
     }

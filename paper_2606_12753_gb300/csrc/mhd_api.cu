@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -178,9 +179,12 @@ struct mhd_handle {
   cudaStream_t s_in = nullptr, s_out = nullptr;
   cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
   long long nstream = 0;                   // streamed steps since the handle was created
+  unsigned long long floors_seen = 0;      // floor hits already reported (MHD_FLOOR_ERROR)
 };
 
-static std::string g_create_err;
+// error text of calls without a handle, one per host thread (calls on
+// different devices may run on several threads at once)
+static thread_local std::string g_create_err;
 
 static int fail(mhd_handle* h, int code, const char* fmt, ...) {
   char buf[512];
@@ -254,6 +258,8 @@ static int validate(const mhd_config* c, mhd_handle* h) {
   if (c->riemann == MHD_LEARNED && (tx != 16 || ty != 8))
     return fail(h, MHD_ERR_INVALID, "the learned switch is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
   if (c->integrator != MHD_RK2 && c->integrator != MHD_RK3) return fail(h, MHD_ERR_INVALID, "unknown integrator");
+  if (c->floor_policy != MHD_FLOOR_COUNT && c->floor_policy != MHD_FLOOR_ERROR)
+    return fail(h, MHD_ERR_INVALID, "unknown floor policy");
   if (c->integrator == MHD_RK3 && (tx != 16 || ty != 8))
     return fail(h, MHD_ERR_INVALID, "SSP-RK3 is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
   if (c->integrator == MHD_RK3 && c->riemann == MHD_LEARNED)
@@ -566,6 +572,15 @@ static int check_status(mhd_handle* h) {
   unsigned st = *(unsigned*)((unsigned long long*)h->pinned + 3);
   if (st & ST_NONFINITE) return fail(h, MHD_ERR_NONFINITE, "non-finite state value met on the device");
   if (st & ST_TIMEOUT) return fail(h, MHD_ERR_TIMEOUT, "device barrier timed out");
+  if (h->cfg.floor_policy == MHD_FLOOR_ERROR) {
+    const unsigned long long* hp = (const unsigned long long*)h->pinned;
+    unsigned long long hits = hp[8 + C_RHO_FLOOR] + hp[8 + C_P_FLOOR];
+    if (hits > h->floors_seen) {
+      unsigned long long rho = hp[8 + C_RHO_FLOOR], p = hp[8 + C_P_FLOOR];
+      h->floors_seen = hits;
+      return fail(h, MHD_ERR_FLOOR, "floors applied: %llu density and %llu pressure hits so far", rho, p);
+    }
+  }
   return MHD_OK;
 }
 
@@ -914,11 +929,14 @@ struct mhd_batch {
   std::vector<mhd_config> cfg;
   std::vector<BoxDesc> box;          // host mirror
   BoxDesc* dbox = nullptr;           // device copy
+  ItemRef* dorder = nullptr;         // device item list, longest first
+  size_t dorder_cap = 0;             // its capacity in entries
   std::vector<size_t> ubytes, kbytes, wbytes;
   std::vector<bool> prims_valid;
   void* pool = nullptr;              // all per-box buffers
   unsigned long long* words = nullptr;   // [0..63] general, then 2 per box
   unsigned* bar_count = nullptr;
+  unsigned long long* work = nullptr;    // item draws of one launch
   unsigned* status = nullptr;
   unsigned long long* counters = nullptr;
   void* pinned = nullptr;
@@ -938,7 +956,7 @@ struct mhd_batch {
   std::string err;
 };
 
-static std::string g_batch_err;
+static thread_local std::string g_batch_err;   // error text of batch calls without a handle, per host thread
 
 static int bfail(mhd_batch* b, int code, const char* fmt, ...) {
   char buf[512];
@@ -988,6 +1006,33 @@ static int batch_apply_tile(mhd_batch* b, int tx, int ty, int tz) {
     item += b->box[i].nitems;
   }
   b->total_items = item;
+  // the item list, longest first: a chunk's cost grows with its planes plus
+  // the three-plane prologue of its z-march (ties keep box order)
+  std::vector<std::pair<int, ItemRef>> items;
+  items.reserve((size_t)item);
+  for (int i = 0; i < b->nbox; ++i) {
+    const Geo& g = b->box[i].g;
+    const int per_chunk = g.ntx * g.nty;
+    for (int l = 0; l < b->box[i].nitems; ++l) {
+      const int kb = (l / per_chunk) * g.TZ;
+      const int ke = kb + g.TZ < g.n[2] ? kb + g.TZ : g.n[2];
+      items.push_back({ke - kb + 3, ItemRef{i, l}});
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<int, ItemRef>& x, const std::pair<int, ItemRef>& y) { return x.first > y.first; });
+  std::vector<ItemRef> order(items.size());
+  for (size_t q = 0; q < items.size(); ++q) order[q] = items[q].second;
+  if (order.size() > b->dorder_cap) {
+    drop_graph(b);
+    cudaFree(b->dorder);
+    b->dorder = nullptr;
+    b->dorder_cap = 0;
+    BCUDA_TRY(b, cudaMalloc(&b->dorder, order.size() * sizeof(ItemRef)));
+    b->dorder_cap = order.size();
+  }
+  BCUDA_TRY(b, cudaMemcpyAsync(b->dorder, order.data(), order.size() * sizeof(ItemRef), cudaMemcpyHostToDevice,
+                               b->stream));
   b->tx = tx; b->ty = ty; b->tz = tz;
   b->smem = smem;
   b->grid = (unsigned)(per_sm * nsm);
@@ -1005,6 +1050,7 @@ extern "C" void mhd_batch_destroy(mhd_batch* b) {
   cudaFree(b->pool);
   cudaFree(b->words);
   cudaFree(b->dbox);
+  cudaFree(b->dorder);
   if (b->pinned) cudaFreeHost(b->pinned);
   delete b;
 }
@@ -1062,6 +1108,7 @@ extern "C" int mhd_batch_create(int nbox, const mhd_config* cfgs, void* cuda_str
     return code;
   }
   b->bar_count = (unsigned*)(b->words + 0);
+  b->work = b->words + 1;
   b->status = (unsigned*)(b->words + 3);
   b->counters = b->words + 8;
   char* pool = (char*)b->pool;
@@ -1154,6 +1201,8 @@ static BatchArgs batch_args(mhd_batch* b, double dt, int nsteps) {
   ba.boxes = b->dbox;
   ba.nbox = b->nbox;
   ba.total_items = b->total_items;
+  ba.order = b->dorder;
+  ba.work = b->work;
   ba.nsteps = nsteps;
   ba.dt = dt;
   ba.bar_count = b->bar_count;
@@ -1174,7 +1223,7 @@ static int batch_enqueue(mhd_batch* b, double dt, int nsteps) {
     drop_graph(b);
     cudaGraph_t gr = nullptr;
     BCUDA_TRY(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(b->bar_count, 0, sizeof(unsigned), b->cap);
+    cudaError_t e = cudaMemsetAsync(b->words, 0, 2 * sizeof(unsigned long long), b->cap);   // barrier, draws
     if (e == cudaSuccess) e = batch_launch(b->prec, b->tx, b->ty, b->grid, b->smem, b->cap, ba);
     if (e == cudaSuccess) {
       batch_advance<<<(b->nbox + 127) / 128, 128, 0, b->cap>>>(b->dbox, b->nbox, nsteps);
@@ -1195,7 +1244,7 @@ static int batch_enqueue(mhd_batch* b, double dt, int nsteps) {
   if (graph) {
     BCUDA_TRY(b, cudaGraphLaunch(b->gexec, b->stream));
   } else {
-    BCUDA_TRY(b, cudaMemsetAsync(b->bar_count, 0, sizeof(unsigned), b->stream));
+    BCUDA_TRY(b, cudaMemsetAsync(b->words, 0, 2 * sizeof(unsigned long long), b->stream));   // barrier, draws
     BCUDA_TRY(b, batch_launch(b->prec, b->tx, b->ty, b->grid, b->smem, b->stream, ba));
     batch_advance<<<(b->nbox + 127) / 128, 128, 0, b->stream>>>(b->dbox, b->nbox, nsteps);
     BCUDA_TRY(b, cudaGetLastError());

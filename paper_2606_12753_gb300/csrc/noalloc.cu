@@ -64,6 +64,9 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, void* cuda_stream, const 
   if (dt != dt) return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s", "dt is NaN");
   if (cfg->integrator != MHD_RK2 || cfg->recon != MHD_RECON_PRIMITIVE)
     return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s", "runs RK2 with primitive reconstruction only");
+  if (cfg->riemann == MHD_LEARNED)
+    return noalloc_fail(MHD_ERR_INVALID, "mhd_step_noalloc: %s",
+                        "runs HLLD or HLL only (the learned switch needs a network on a handle)");
   int rc = internal_validate(cfg);
   if (rc) return rc;   // message already set
   Geo g;

@@ -1114,7 +1114,8 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char
 // Primitives (and the CFL max) of a state set from outside.  One CTA per
 // (j, k) row of cells, threads along x: the row's index math is one division
 // per CTA, and a cell's faces are its own (the face above the last cell of a
-// periodic axis is face 0), so no ghost logic is needed.
+// periodic axis is face 0), so no ghost logic is needed.  Floor hits count
+// like those of the stage kernels' recoveries.
 template <int PREC>
 __global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
   using R = typename Prec<PREC>::R;
@@ -1132,6 +1133,7 @@ __global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
   const long long xbase = g.face_off[0] + (long long)g.nf[0] * row;
   R smax = R(0);
   bool bad = false;
+  unsigned nrho = 0, np = 0;
   (void)nz;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const long long s = i + (long long)nx * row;
@@ -1141,6 +1143,8 @@ __global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
     recover<PREC>(g, (double)U[s], (double)U[g.ncell + s], (double)U[2 * g.ncell + s], (double)U[3 * g.ncell + s],
                   (double)U[4 * g.ncell + s], (double)U[xbase + i], (double)U[xbase + ih], (double)U[ybase_lo + i],
                   (double)U[ybase_hi + i], (double)U[zbase_lo + i], (double)U[zbase_hi + i], w, hr, hp);
+    nrho += hr;
+    np += hp;
     if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
 #pragma unroll
     for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
@@ -1149,11 +1153,15 @@ __global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
   }
   const unsigned mask = 0xffffffffu;
   const unsigned anybad = __any_sync(mask, bad);
+  nrho = __reduce_add_sync(mask, nrho);
+  np = __reduce_add_sync(mask, np);
   double sm64 = (double)smax;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sm64 = fmax(sm64, __shfl_xor_sync(mask, sm64, o));
   if ((threadIdx.x & 31) == 0) {
     if (anybad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    if (nrho) atomicAdd(&a.counters[C_RHO_FLOOR], (unsigned long long)nrho);
+    if (np) atomicAdd(&a.counters[C_P_FLOOR], (unsigned long long)np);
     if (sm64 > 0.0) atomicMax(a.nextword, (unsigned long long)__double_as_longlong(sm64));
   }
 }

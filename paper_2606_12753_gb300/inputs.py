@@ -388,3 +388,116 @@ def brio_wu(n: int = 256, axis: int = 0, gamma: float = 2.0) -> Box:
     zero = np.zeros(shape)
     cell = conserved(rho, (zero, zero, zero), p, face, tuple(dims), tuple(bc), gamma)
     return Box(nx, ny, nz, h, h, h, tuple(bc), gamma, cell, face, name=f"brio_wu_{n}")
+
+
+# --------------------------------------------------------------------------
+# edge cases of the method (verification states)
+# --------------------------------------------------------------------------
+
+def _smooth_fields(dims, rng, count, nmodes=5):
+    """`count` smooth periodic random fields on the cell centres, each of unit
+    rms order, from a few seeded Fourier modes along the axes with >1 cell."""
+    nx, ny, nz = dims
+    x, y, z = _centres(dims)
+    L = np.array([nx, ny, nz], dtype=np.float64)
+    out = []
+    for _ in range(count):
+        f = np.zeros((nz, ny, nx))
+        for _m in range(nmodes):
+            k = rng.integers(-3, 4, size=3).astype(np.float64)
+            for d in range(3):
+                if dims[d] == 1:
+                    k[d] = 0.0
+            f += rng.standard_normal() * np.sin(2 * np.pi * (k[0] * x / L[0] + k[1] * y / L[1] + k[2] * z / L[2])
+                                                 + rng.uniform(0, 2 * np.pi))
+        out.append(f / math.sqrt(nmodes))
+    return out
+
+
+def supersonic_state(dims, seed: int, v0=(4.0, -4.0, 4.0), gamma: float = GAMMA) -> Box:
+    """Smooth random state (rho ~ 1, p ~ 0.8, |B| ~ 0.5) moving with the
+    uniform velocity v0, well above the fast speed (~1.3) along every axis:
+    the x and z faces take the left outer state (S_L > 0), the y faces the
+    right one (S_R < 0).  Periodic."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    h = 1.0 / max(dims)
+    fr, fp, fvx, fvy, fvz = _smooth_fields(dims, rng, 5)
+    rho = 1.0 + 0.2 * np.tanh(fr)
+    p = 0.8 + 0.2 * np.tanh(fp)
+    v = (v0[0] + 0.3 * fvx, v0[1] + 0.3 * fvy, v0[2] + 0.3 * fvz)
+    bc = (PERIODIC,) * 3
+    b0 = (0.3, -0.2, 0.4)
+    face = [np.full((nz, ny, nx), b0[d]) for d in range(3)]
+    cell = conserved(rho, v, p, face, dims, bc, gamma)
+    return Box(nx, ny, nz, h, h, h, bc, gamma, cell, face, name=f"supersonic_{nx}x{ny}x{nz}_{seed}")
+
+
+def transverse_field_state(dims, seed: int, gamma: float = GAMMA) -> Box:
+    """State whose field is purely along z and varies only in x and y, with
+    rho, p and v also independent of z: B_n = 0 on every x and y face (the
+    HLLD double-star region collapses there), and B_x = B_y = 0 for all
+    time.  Periodic."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    h = 1.0 / max(dims)
+    d2 = (nx, ny, 1)
+    fr, fp, fvx, fvy, fvz, fb = _smooth_fields(d2, rng, 6)
+    rep = lambda a: np.ascontiguousarray(np.repeat(a, nz, axis=0))
+    rho = rep(1.0 + 0.3 * np.tanh(fr))
+    p = rep(0.7 + 0.3 * np.tanh(fp))
+    v = (rep(0.8 * fvx), rep(0.8 * fvy), rep(0.5 * fvz))
+    bz = rep(0.8 + 0.4 * np.tanh(fb))
+    bc = (PERIODIC,) * 3
+    face = [np.zeros((nz, ny, nx)), np.zeros((nz, ny, nx)), bz]
+    cell = conserved(rho, v, p, face, dims, bc, gamma)
+    return Box(nx, ny, nz, h, h, h, bc, gamma, cell, face, name=f"transverse_{nx}x{ny}x{nz}_{seed}")
+
+
+def alfvenic_shear_state(dims, seed: int, b0: float = 1.0, p0: float = 0.1, gamma: float = GAMMA) -> Box:
+    """Uniform rho = 1 and p = p0 at rest along x, field B = (b0, 0, 0) with
+    the Alfven speed b0 above the sound speed, and transverse velocities
+    v_y(x, z), v_z(x, y): every x face has equal outer states but for its
+    tangential velocity, B_t = 0 and a fast speed equal to the Alfven speed,
+    the degenerate star state of HLLD (den = 0 up to rounding).  The y and z
+    faces have B_n = 0.  Periodic."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    h = 1.0 / max(dims)
+    x, y, z = _centres(dims)
+    L = np.array([nx, ny, nz], dtype=np.float64)
+    f1, f2 = _smooth_fields((nx, 1, nz), rng, 1)[0], _smooth_fields((nx, ny, 1), rng, 1)[0]
+    vy = 0.3 * np.broadcast_to(f1, (nz, ny, nx)) if ny > 1 or nz > 1 else 0.3 * f1
+    vz = 0.3 * np.broadcast_to(f2, (nz, ny, nx))
+    shape = (nz, ny, nx)
+    bc = (PERIODIC,) * 3
+    face = [np.full(shape, b0), np.zeros(shape), np.zeros(shape)]
+    cell = conserved(np.ones(shape), (np.zeros(shape), np.ascontiguousarray(vy), np.ascontiguousarray(vz)),
+                     np.full(shape, p0), face, dims, bc, gamma)
+    return Box(nx, ny, nz, h, h, h, bc, gamma, cell, face, name=f"alfvenic_shear_{nx}x{ny}x{nz}_{seed}")
+
+
+def near_floor_state(dims, seed: int, bc=(OUTFLOW,) * 3, gamma: float = GAMMA, floor_cells: int = 4) -> Box:
+    """Density spanning 1e-8 .. 1 (log-smooth), temperature p/rho ~ 0.5, slow
+    flow (|v| ~ 0.1) and a weak uniform field (|B| = 1e-5), so that thermal
+    energy dominates even at the lowest densities; in `floor_cells` seeded
+    cells of the lowest-density tenth the total energy is set to half the
+    kinetic energy, so their recovered pressure is negative and takes the
+    pressure floor."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    h = 1.0 / max(dims)
+    fr, ft, fvx, fvy, fvz = _smooth_fields(dims, rng, 5)
+    rho = 10.0 ** (-4.0 + 4.0 * np.tanh(1.5 * fr))
+    p = rho * (0.5 + 0.2 * np.tanh(ft))
+    v = (0.1 * fvx, 0.1 * fvy, 0.1 * fvz)
+    b = (1e-5 * 0.6, -1e-5 * 0.64, 1e-5 * 0.48)
+    shapes = [(nz, ny, nx + (bc[0] == OUTFLOW)), (nz, ny + (bc[1] == OUTFLOW), nx), (nz + (bc[2] == OUTFLOW), ny, nx)]
+    face = [np.full(shapes[d], b[d]) for d in range(3)]
+    cell = conserved(rho, v, p, face, dims, bc, gamma)
+    low = np.flatnonzero(rho.ravel() <= np.quantile(rho, 0.1))
+    for s in rng.choice(low, size=min(floor_cells, low.size), replace=False):
+        k, j, i = np.unravel_index(s, rho.shape)
+        ke = 0.5 * (cell[1, k, j, i] ** 2 + cell[2, k, j, i] ** 2 + cell[3, k, j, i] ** 2) / cell[0, k, j, i]
+        cell[4, k, j, i] = 0.5 * ke
+    return Box(nx, ny, nz, h, h, h, tuple(bc), gamma, cell, face, name=f"near_floor_{nx}x{ny}x{nz}_{seed}")

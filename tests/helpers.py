@@ -4,7 +4,18 @@ import numpy as np
 import oracle as O
 
 
-def ocfg(b, **kw):
+def thresholds(precision):
+    """The oracle's branch thresholds for a GPU form: the FP32-bulk forms
+    (mixed, fp32) take the HLLD-degeneracy, mass-flux-deadband and
+    characteristic-degeneracy decisions at 1e-6, the FP64 form at 1e-12,
+    1e-10, 1e-12."""
+    return O.THRESH_FP32 if precision in ("mixed", "fp32") else O.THRESH_FP64
+
+
+def ocfg(b, precision=None, **kw):
+    """Oracle config of a box; `precision` (the GPU form it is compared with)
+    selects the branch thresholds."""
+    kw.setdefault("thresholds", thresholds(precision))
     return O.Config(b.nx, b.ny, b.nz, b.dx, b.dy, b.dz, b.gamma, getattr(b, "cfl", 0.4), tuple(b.bc), **kw)
 
 
@@ -41,10 +52,10 @@ def state_errors(cell, face, ref_cell, ref_face):
     return errs
 
 
-def subbox(cell, face, n, center, h, dx, gamma):
+def subbox(cell, face, n, center, h, dx, gamma, precision=None):
     """Outflow sub-box of (2h+1)^3 cells around center = (i, j, k), cut from a
     periodic state of n = (nx, ny, nz) cells (indices wrap).  Returns (Config,
-    cell, face) for the oracle."""
+    cell, face) for the oracle, with the branch thresholds of `precision`."""
     i, j, k = center
     nx, ny, nz = n
     xi = np.arange(i - h, i + h + 1) % nx
@@ -58,5 +69,39 @@ def subbox(cell, face, n, center, h, dx, gamma):
     by = np.ascontiguousarray(face[1][zk][:, yf][:, :, xi])
     bz = np.ascontiguousarray(face[2][zf][:, yj][:, :, xi])
     m = 2 * h + 1
-    cfg = O.Config(m, m, m, dx[0], dx[1], dx[2], gamma, 0.4, (O.OUTFLOW,) * 3)
+    cfg = O.Config(m, m, m, dx[0], dx[1], dx[2], gamma, 0.4, (O.OUTFLOW,) * 3, thresholds=thresholds(precision))
     return cfg, c, [bx, by, bz]
+
+
+def max_elementwise_rel(cell, face, ref_cell, ref_face, floor_frac=1e-6):
+    """Largest per-element relative error over all 8 variables:
+    |q - ref| / max(|ref|, floor_frac x scale), where the scale of rho and E
+    is their own largest magnitude and the scale of a momentum or field
+    component is the largest magnitude of any component of that vector (a
+    component that is zero up to rounding, such as B_z of a 1D tube, is not
+    divided by its own rounding noise).  Returns (worst value, variable name,
+    flat index)."""
+    names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz"]
+    arrs = [(np.asarray(cell[v], np.float64), np.asarray(ref_cell[v], np.float64)) for v in range(5)]
+    arrs += [(np.asarray(face[d], np.float64), np.asarray(ref_face[d], np.float64)) for d in range(3)]
+    top_of = lambda a: float(np.abs(a).max()) if a.size else 0.0
+    m_top = max(top_of(arrs[v][1]) for v in (1, 2, 3))
+    b_top = max(top_of(arrs[v][1]) for v in (5, 6, 7))
+    worst = (0.0, "", -1)
+    for v, (name, (q, r)) in enumerate(zip(names, arrs)):
+        top = m_top if v in (1, 2, 3) else (b_top if v >= 5 else top_of(r))
+        den = np.maximum(np.abs(r), floor_frac * top) if top > 0 else np.ones_like(r)
+        e = np.abs(q - r) / den
+        i = int(np.argmax(e)) if e.size else -1
+        if e.size and float(e.flat[i]) > worst[0]:
+            worst = (float(e.flat[i]), name, i)
+    return worst
+
+
+def perturbed(cell, face, rel=6e-8, seed=0):
+    """The state with every value multiplied by (1 + rel xi), xi = +-1 seeded:
+    FP32 rounding-sized noise (half an FP32 ulp is 6e-8 relative)."""
+    rng = np.random.default_rng(seed)
+    c = np.asarray(cell, np.float64) * (1.0 + rel * rng.choice([-1.0, 1.0], size=np.shape(cell)))
+    f = [np.asarray(x, np.float64) * (1.0 + rel * rng.choice([-1.0, 1.0], size=np.shape(x))) for x in face]
+    return np.ascontiguousarray(c), [np.ascontiguousarray(x) for x in f]

@@ -42,7 +42,7 @@ def test_default_config_host_only():
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("gamma", 1.0), ("cfl", 0.0), ("precision", 7),
                                          ("riemann", 9), ("emf", 3), ("rho_floor", 0.0), ("tile_x", 65),
-                                         ("tile_y", -1)])
+                                         ("tile_y", -1), ("floor_policy", 2)])
 def test_invalid_config_rejected(field, value):
     c = mhd.mhd_default_config(16, 16, 16)
     setattr(c, field, value)
@@ -186,3 +186,41 @@ def test_null_handles_and_arguments_are_rejected():
     L.mhd_batch_last_error.restype = C.c_char_p
     assert L.mhd_last_error(P) is not None
     assert L.mhd_batch_last_error(P) is not None
+
+
+def test_noalloc_rejects_the_learned_switch_on_the_host():
+    """The allocation-free step runs HLLD or HLL; a learned-switch config is
+    refused with its own message before any CUDA call."""
+    c = mhd.mhd_default_config(8, 8, 8)
+    c.riemann = mhd.MHD_LEARNED
+    with pytest.raises(mhd.MHDError) as ei:
+        mhd.mhd_step_noalloc(c, [1] * 5, [1] * 3, [1] * 5, [1] * 3, 1e-3)
+    assert ei.value.code == mhd.MHD_ERR_INVALID
+    assert "learned" in mhd.mhd_last_error(None)
+
+
+def test_error_text_without_a_handle_is_per_thread():
+    """A failed call without a handle leaves its text on its own host thread."""
+    import threading
+    c = mhd.mhd_default_config(16, 16, 16)
+    c.gamma = 1.0
+    with pytest.raises(mhd.MHDError):
+        mhd.mhd_create(c)
+    mine = mhd.mhd_last_error(None)
+    seen = {}
+
+    def other():
+        seen["before"] = mhd.mhd_last_error(None)
+        c2 = mhd.mhd_default_config(16, 16, 16)
+        c2.cfl = 0.0
+        try:
+            mhd.mhd_create(c2)
+        except mhd.MHDError:
+            pass
+        seen["after"] = mhd.mhd_last_error(None)
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert "gamma" in mine and seen["before"] == "" and "cfl" in seen["after"]
+    assert mhd.mhd_last_error(None) == mine

@@ -102,3 +102,22 @@ def test_profile_record_carries_the_instruction_count():
     if rec is not None:   # captured for the current sources
         assert float(rec["warp_inst_per_launch"]) > 0 and float(rec["dram_bytes_per_launch"]) > 0
     assert bench.ISSUE_PEAK_WARP_INST_PER_S == pytest.approx(152 * 4 * 2.07e9)
+
+
+def test_minimum_bytes_are_the_conserved_states():
+    """The roofline's bytes per cell-update: the conserved states read and
+    written once per stage (FP64 8-value states; the mixed form's U* and the
+    FP32 form in 4-byte values), halos from cache."""
+    for prec, total in (("fp64", 320), ("mixed", 256), ("fp32", 160)):
+        assert sum(bench.MIN_STAGE_BYTES[prec]) == total
+    s1, s2 = bench.MIN_STAGE_BYTES["mixed"]
+    assert s1 == 8 * 8 + 8 * 4 and s2 == 8 * 4 + 8 * 8 + 8 * 8
+    # the design's stored primitives only add bytes
+    for prec in ("fp64", "mixed", "fp32"):
+        assert all(d > m for d, m in zip(bench.STAGE_BYTES[prec], bench.MIN_STAGE_BYTES[prec]))
+
+
+def test_oracle_throughput_counts_every_process():
+    rate, cells, el = bench.oracle_throughput(8, 2, 1, 2)
+    assert cells == 2 * 2 * 8 ** 3 and el > 0
+    assert rate == pytest.approx(cells / el / 1e6)

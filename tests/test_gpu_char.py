@@ -42,7 +42,7 @@ def test_char_fp64_matches_oracle(bc):
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
 def test_char_reduced_precision_matches_oracle(precision):
     box = I.random_state((37, 21, 13), seed=42, bc=(0, 0, 0))
-    cfg = ocfg(box, recon=1)
+    cfg = ocfg(box, precision, recon=1)
     dt = O.cfl_dt(cfg, box.cell, box.face)
     c, f = _gpu_steps(box, precision, [dt, dt])
     rc, rf = O.step_dts(cfg, box.cell, box.face, [dt, dt])
@@ -54,7 +54,7 @@ def test_char_reduced_precision_matches_oracle(precision):
 def test_char_operator_matches_oracle(precision):
     from paper_2606_12753_gb300 import mhd
     box = I.random_state((29, 21, 13), seed=43, bc=(0, 0, 0), noise=0.0)
-    du, db = O.rhs(ocfg(box, recon=1), box.cell, box.face)
+    du, db = O.rhs(ocfg(box, precision, recon=1), box.cell, box.face)
     s = mhd.Solver(box, precision=precision, recon="characteristic", tile=(16, 8, 6))
     s.set_state(box.cell, box.face)
     gc, gf = s.rhs()

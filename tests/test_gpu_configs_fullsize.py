@@ -12,14 +12,16 @@ times (default tiles):
   persistent launch), one step with one explicit dt: sampled cells of several
   boxes against the oracle on sub-boxes clamped to each box (a side that
   meets the box edge is the box's own outflow boundary, the others lie 5
-  cells from the sample), relative L1 1e-5 x kappa (the batch's reading of
-  the FP32 bar for ill-conditioned pressure recovery, test_gpu_batch.py)."""
+  cells from the sample), relative L1 per variable within max(1e-5, 3 x the
+  movement of the oracle's own result when its input carries FP32-rounding-
+  sized noise, 6e-8 relative): these low-beta boxes recover their pressure
+  ill-conditioned, and the control measures by how much."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2606_12753_gb300 import inputs as I
-from helpers import ocfg, state_errors, subbox
+from helpers import ocfg, perturbed, state_errors, subbox
 
 pytestmark = pytest.mark.gpu
 
@@ -79,7 +81,8 @@ def test_orszag_tang_3d_512_step_sampled_mixed():
     h = 7
     got_c, ref_c, got_f, ref_f = [], [], [], []
     for (i, j, k) in pts:
-        cfg, cell, face = subbox(box.cell, box.face, (n, n, n), (i, j, k), h, (box.dx, box.dy, box.dz), box.gamma)
+        cfg, cell, face = subbox(box.cell, box.face, (n, n, n), (i, j, k), h, (box.dx, box.dy, box.dz), box.gamma,
+                                 "mixed")
         r_c, r_f = O.step_dts(cfg, cell, face, [dt])
         ref_c.append(r_c[:, h, h, h])
         got_c.append(c[:, k, j, i])
@@ -101,7 +104,7 @@ def _clamped_subbox(box, centre, h):
     by = np.ascontiguousarray(box.face[1][sz, lo[1]:hi[1] + 1, sx])
     bz = np.ascontiguousarray(box.face[2][lo[2]:hi[2] + 1, sy, sx])
     cfg = O.Config(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], box.dx, box.dy, box.dz, box.gamma, 0.4,
-                   (O.OUTFLOW,) * 3)
+                   (O.OUTFLOW,) * 3, thresholds=O.THRESH_FP32)
     return cfg, cell, [bx, by, bz], tuple(centre[d] - lo[d] for d in range(3))
 
 
@@ -134,15 +137,22 @@ def test_blast_batch64_step_sampled_fp32():
         n = (bx.nx, bx.ny, bx.nz)
         pts = [(0, 0, 0), (n[0] - 1, n[1] - 1, n[2] - 1), (n[0] // 2, n[1] // 2, n[2] // 2), (15, 7, min(31, n[2] - 1))]
         pts += [tuple(int(rng.integers(0, n[d])) for d in range(3)) for _ in range(4)]
-        got_c, ref_c, got_f, ref_f = [], [], [], []
+        got_c, ref_c, got_f, ref_f, mov_c, mov_f = [], [], [], [], [], []
         for (i, j, k) in pts:
             i, j, k = min(i, n[0] - 1), min(j, n[1] - 1), min(k, n[2] - 1)
             cfg, cell, face, (ci, cj, ck) = _clamped_subbox(bx, (i, j, k), h)
             r_c, r_f = O.step_dts(cfg, cell, face, [dt])
+            p_c, p_f = O.step_dts(cfg, *perturbed(cell, face, seed=bi * 100 + i), [dt])
+            mov_c.append(p_c[:, ck, cj, ci])
+            mov_f.append([p_f[0][ck, cj, ci], p_f[1][ck, cj, ci], p_f[2][ck, cj, ci]])
             ref_c.append(r_c[:, ck, cj, ci])
             got_c.append(c[:, k, j, i])
             ref_f.append([r_f[0][ck, cj, ci], r_f[1][ck, cj, ci], r_f[2][ck, cj, ci]])
             got_f.append([f[0][k, j, i], f[1][k, j, i], f[2][k, j, i]])
         errs = _sampled_errors(got_c, ref_c, got_f, ref_f)
-        assert max(errs.values()) <= 1e-5 * _kappa(bx), (bi, bx.name, errs)
+        # control: how far FP32-rounding-sized input noise moves the oracle
+        move = _sampled_errors(mov_c, ref_c, mov_f, ref_f)
+        over = {k: (errs[k], move[k]) for k in errs if not errs[k] <= max(1e-5, 3.0 * move[k])}
+        print(bx.name, "kappa", round(_kappa(bx)), "error", max(errs.values()), "oracle movement", max(move.values()))
+        assert not over, (bi, bx.name, over)
     b.close()

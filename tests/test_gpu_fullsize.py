@@ -46,8 +46,8 @@ def _samples(seed=2606, nrand=24):
     return pts
 
 
-def _subbox(box, center, h):
-    return subbox(box.cell, box.face, (N, N, N), center, h, (box.dx, box.dy, box.dz), box.gamma)
+def _subbox(box, center, h, precision=None):
+    return subbox(box.cell, box.face, (N, N, N), center, h, (box.dx, box.dy, box.dz), box.gamma, precision)
 
 
 def _rel_l1(got, ref):
@@ -99,7 +99,7 @@ def test_operator_at_256_sampled(smooth, precision):
     got_c, ref_c, got_f, ref_f = [], [], [], []
     h = 4
     for (i, j, k) in _samples():
-        cfg, cell, face = _subbox(box, (i, j, k), h)
+        cfg, cell, face = _subbox(box, (i, j, k), h, precision)
         du, db = O.rhs(cfg, cell, face)
         ref_c.append(du[:, h, h, h])
         got_c.append(gc[:, k, j, i])
@@ -123,7 +123,7 @@ def test_step_at_256_sampled(box, smooth, state, precision):
     got_c, ref_c, got_f, ref_f = [], [], [], []
     h = 7
     for (i, j, k) in _samples(nrand=12):
-        cfg, cell, face = _subbox(start, (i, j, k), h)
+        cfg, cell, face = _subbox(start, (i, j, k), h, precision)
         rc, rf = O.step_dts(cfg, cell, face, [dt])
         ref_c.append(rc[:, h, h, h])
         got_c.append(c[:, k, j, i])
@@ -169,7 +169,7 @@ def test_learned_operator_at_256_sampled(smooth):
     got_c, ref_c, got_f, ref_f = [], [], [], []
     h = 4
     for (i, j, k) in _samples():
-        cfg, cell, face = _subbox(box, (i, j, k), h)
+        cfg, cell, face = _subbox(box, (i, j, k), h, "mixed")
         xi, yj, zk = [(np.arange(c - h, c + h + 1)) % N for c in (i, j, k)]
         cfg.riemann = O.MASK
         cfg.choice = np.ascontiguousarray(choice[:, zk][:, :, yj][:, :, :, xi]).reshape(-1)
@@ -203,7 +203,7 @@ def test_rk3_step_at_352_sampled(precision):
     h = 7
     for (i, j, k) in pts:
         cfg, cell, face = subbox(start.cell, start.face, (n, n, n), (i, j, k), h, (start.dx, start.dy, start.dz),
-                                 start.gamma)
+                                 start.gamma, precision)
         cfg.integrator = "rk3"
         rc, rf = O.step_dts(cfg, cell, face, [dt])
         ref_c.append(rc[:, h, h, h])

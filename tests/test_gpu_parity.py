@@ -29,7 +29,7 @@ def run_gpu(box, dts, precision="fp64", **kw):
 
 
 def check(box, nsteps, precision, tol=None, emf=0, **kw):
-    cfg = ocfg(box, emf_mean=emf)
+    cfg = ocfg(box, precision, emf_mean=emf)
     dt = O.cfl_dt(cfg, box.cell, box.face)
     dts = [dt * (1.0 - 0.05 * s) for s in range(nsteps)]
     rc, rf = O.step_dts(cfg, box.cell, box.face, dts)
@@ -160,9 +160,10 @@ def test_nonfinite_is_reported():
 
 
 def test_floor_hits_are_counted():
-    """Floors are counted where primitives are recovered.  The oracle recovers
-    U^n and U* in each step; the fused kernels recover U* and U^{n+1} at the
-    end of each stage, so over one step GPU = oracle - hits(U^0) + hits(U^1)."""
+    """Floors are counted wherever primitives are recovered.  The oracle
+    recovers U^n and U* in each step; the GPU recovers the state set from the
+    host (U^0) once, then U* and U^{n+1} at the end of each stage, so over one
+    step GPU = oracle + hits(U^1)."""
     from paper_2606_12753_gb300 import mhd
     box = I.random_state((16, 12, 8), seed=52)
     cell = box.cell.copy()
@@ -180,7 +181,8 @@ def test_floor_hits_are_counted():
     st = s.stats()
     s.close()
     assert st_step.p_floor_hits >= 2
-    assert st["p_floor_hits"] == st_step.p_floor_hits - st0.p_floor_hits + st1.p_floor_hits
+    assert st0.p_floor_hits >= 2
+    assert st["p_floor_hits"] == st_step.p_floor_hits + st1.p_floor_hits
 
 
 RHS_TOL = {"fp64": 1e-12, "mixed": 1e-5, "fp32": 1e-5}
@@ -193,7 +195,7 @@ def test_spatial_operator_parity(precision, bc):
     -curl E -- element by element against the oracle's operator."""
     from paper_2606_12753_gb300 import mhd
     box = I.random_state((29, 21, 13), seed=61, bc=bc, noise=0.0)
-    cfg = ocfg(box)
+    cfg = ocfg(box, precision)
     du, db = O.rhs(cfg, box.cell, box.face)
     s = mhd.Solver(box, precision=precision, tile=(16, 8, 6))
     s.set_state(box.cell, box.face)

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from paper_2606_12753_gb300 import inputs as I
-from helpers import ocfg, state_errors
+from helpers import ocfg, state_errors, thresholds
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def _run(box, precision, dts):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_riemann2d_hll_matches_oracle(precision):
     box = I.riemann_2d(97, seed=8)
-    cfg = ocfg(box, riemann=O.HLL)
+    cfg = ocfg(box, precision, riemann=O.HLL)
     dt = O.cfl_dt(cfg, box.cell, box.face)
     dts = [dt] * 4
     c, f = _run(box, precision, dts)
@@ -36,7 +36,7 @@ def test_riemann2d_hll_matches_oracle(precision):
     assert max(errs.values()) <= (1e-12 if precision == "fp64" else 1e-5), errs
 
 
-def _subbox2d(box, centre, h):
+def _subbox2d(box, centre, h, precision=None):
     i, j = centre
     n = box.nx
     lo_x, hi_x = max(0, i - h), min(n, i + h + 1)
@@ -46,7 +46,7 @@ def _subbox2d(box, centre, h):
     by = np.ascontiguousarray(box.face[1][:, lo_y:hi_y + 1, lo_x:hi_x])
     bz = np.ascontiguousarray(box.face[2][:, lo_y:hi_y, lo_x:hi_x])
     cfg = O.Config(hi_x - lo_x, hi_y - lo_y, 1, box.dx, box.dy, box.dz, box.gamma, 0.4,
-                   (O.OUTFLOW, O.OUTFLOW, O.PERIODIC), riemann=O.HLL)
+                   (O.OUTFLOW, O.OUTFLOW, O.PERIODIC), riemann=O.HLL, thresholds=thresholds(precision))
     return cfg, cell, [bx, by, bz], (i - lo_x, j - lo_y)
 
 
@@ -67,7 +67,7 @@ def test_riemann2d_hll_at_3200_sampled(precision):
     pts += [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(12)]
     got_c, ref_c, got_f, ref_f = [], [], [], []
     for (i, j) in pts:
-        cfg, cell, face, (ci, cj) = _subbox2d(box, (i, j), 7)
+        cfg, cell, face, (ci, cj) = _subbox2d(box, (i, j), 7, precision)
         rc, rf = O.step_dts(cfg, cell, face, [dt])
         ref_c.append(rc[:, 0, cj, ci])
         got_c.append(c[:, 0, j, i])

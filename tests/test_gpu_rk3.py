@@ -31,8 +31,8 @@ def _gpu(box, precision, dts=None, nsteps=None, tile=(16, 8, 6)):
     return out, used
 
 
-def _oracle(box, dts):
-    cfg = ocfg(box, integrator="rk3")
+def _oracle(box, dts, precision=None):
+    cfg = ocfg(box, precision, integrator="rk3")
     return O.step_dts(cfg, box.cell, box.face, dts)
 
 
@@ -53,7 +53,7 @@ def test_rk3_reduced_precision_matches_oracle(precision):
     dt = O.cfl_dt(ocfg(box), box.cell, box.face)
     dts = [dt, dt]
     (c, f), _ = _gpu(box, precision, dts)
-    rc, rf = _oracle(box, dts)
+    rc, rf = _oracle(box, dts, precision)
     errs = state_errors(c, f, rc, rf)
     assert max(errs.values()) <= 1e-5, errs
 

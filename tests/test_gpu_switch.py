@@ -115,7 +115,7 @@ def test_switch_choices_and_operator_match_the_oracle(precision):
     assert clear.mean() > 0.9, (clear.mean(), d.max())
     assert 0.3 < ch.mean() < 0.7
     # L(U) with the kernel's choices against the oracle operator with the same choices
-    mcfg = ocfg(box, riemann=O.MASK, choice=ch)
+    mcfg = ocfg(box, precision, riemann=O.MASK, choice=ch)
     st = O.Stats()
     du, db = O.rhs(mcfg, box.cell, box.face, st)
     assert st.faces_hlld == int(ch.sum())
