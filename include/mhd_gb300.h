@@ -86,6 +86,9 @@ extern "C" {
 #define MHD_EMF_UPWIND 0 /* Gardiner & Stone (2005) upwind contact average */
 #define MHD_EMF_MEAN 1   /* arithmetic mean of the four face EMFs (debug) */
 
+#define MHD_COPY_AUTO 0   /* planes of interior tiles arrive by TMA where the kernel supports it (default) */
+#define MHD_COPY_GATHER 1 /* every plane by the per-element gather (same results, bit for bit) */
+
 #define MHD_FLOOR_COUNT 0 /* floors are applied and counted (mhd_get_stats); calls succeed (default) */
 #define MHD_FLOOR_ERROR 1 /* as COUNT, and a synchronising single-box call returns MHD_ERR_FLOOR when the
                              floor counters rose since the previous synchronising call */
@@ -105,6 +108,7 @@ typedef struct {
   int integrator;          /* MHD_RK2 | MHD_RK3 */
   int recon;               /* MHD_RECON_PRIMITIVE | MHD_RECON_CHARACTERISTIC */
   int floor_policy;        /* MHD_FLOOR_COUNT | MHD_FLOOR_ERROR */
+  int plane_copy;          /* MHD_COPY_AUTO | MHD_COPY_GATHER */
 } mhd_config;
 
 typedef struct {
@@ -117,6 +121,7 @@ typedef struct {
   double last_dt;           /* dt of the last step taken */
   int status;               /* device status word (bit 0 non-finite, bit 1 timeout) */
   int steps;                /* steps taken since creation */
+  long long tma_planes;     /* tile planes that arrived by TMA (MHD_COPY_AUTO, interior tiles) */
 } mhd_stats;
 
 typedef struct mhd_handle mhd_handle;

@@ -106,7 +106,7 @@ __device__ __forceinline__ StageArgs box_stage_args(const BatchArgs& ba, const B
 // draw of stage e + 1 starts before the barrier that ends stage e.
 template <int PREC, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 3) batch_kernel(BatchArgs ba) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long next_item;
   const unsigned long long per_stage = (unsigned long long)ba.total_items + gridDim.x;
   unsigned epoch = 0;

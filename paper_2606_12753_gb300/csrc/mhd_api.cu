@@ -1,4 +1,5 @@
 // C ABI of the MHD hot path: handle, device buffers, launches, reductions.
+#include <cuda.h>   // tensor-map types; the encoder itself is fetched from the driver at run time
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -15,9 +16,12 @@
 #include "batch.cuh"
 
 namespace mhd {
-cudaError_t launch_stage_fp64(int, int, int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
-cudaError_t launch_stage_mixed(int, int, int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
-cudaError_t launch_stage_fp32(int, int, int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_fp64(int, int, int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&,
+                                const TmaMaps&);
+cudaError_t launch_stage_mixed(int, int, int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&,
+                                const TmaMaps&);
+cudaError_t launch_stage_fp32(int, int, int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&,
+                                const TmaMaps&);
 cudaError_t set_smem_fp64(int, int, size_t);
 cudaError_t set_smem_mixed(int, int, size_t);
 cudaError_t set_smem_fp32(int, int, size_t);
@@ -25,14 +29,17 @@ size_t smem_bytes_fp64(int, int);
 size_t smem_bytes_mixed(int, int);
 size_t smem_bytes_fp32(int, int);
 size_t smem_bytes_char_fp64();
+size_t smem_bytes_learned_fp64();
 size_t smem_bytes_char_mixed();
+size_t smem_bytes_learned_mixed();
 size_t smem_bytes_char_fp32();
+size_t smem_bytes_learned_fp32();
 cudaError_t launch_stage_learned_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_stage_learned_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
 cudaError_t launch_stage_learned_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
-cudaError_t launch_stage_rk3_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
-cudaError_t launch_stage_rk3_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
-cudaError_t launch_stage_rk3_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&);
+cudaError_t launch_stage_rk3_fp64(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&, const TmaMaps&);
+cudaError_t launch_stage_rk3_mixed(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&, const TmaMaps&);
+cudaError_t launch_stage_rk3_fp32(int, unsigned, size_t, cudaStream_t, const Geo&, const StageArgs&, const TmaMaps&);
 cudaError_t set_smem_rk3_fp64(size_t);
 cudaError_t set_smem_rk3_mixed(size_t);
 cudaError_t set_smem_rk3_fp32(size_t);
@@ -50,12 +57,14 @@ cudaError_t launch_prims_mixed(unsigned, cudaStream_t, const Geo&, const StageAr
 cudaError_t launch_prims_fp32(unsigned, cudaStream_t, const Geo&, const StageArgs&);
 
 cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nb, size_t smem, cudaStream_t st,
-                         const Geo& g, const StageArgs& a) {
+                         const Geo& g, const StageArgs& a, const TmaMaps* tm) {
+  static const TmaMaps no_tma = {};
+  const TmaMaps& maps = tm ? *tm : no_tma;
   if (stage >= ST_RK3_1) {
     switch (prec) {
-      case P_FP64: return launch_stage_rk3_fp64(stage, nb, smem, st, g, a);
-      case P_MIXED: return launch_stage_rk3_mixed(stage, nb, smem, st, g, a);
-      default: return launch_stage_rk3_fp32(stage, nb, smem, st, g, a);
+      case P_FP64: return launch_stage_rk3_fp64(stage, nb, smem, st, g, a, maps);
+      case P_MIXED: return launch_stage_rk3_mixed(stage, nb, smem, st, g, a, maps);
+      default: return launch_stage_rk3_fp32(stage, nb, smem, st, g, a, maps);
     }
   }
   if (g.recon == 1) {
@@ -75,9 +84,9 @@ cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nb, size_
     }
   }
   switch (prec) {
-    case P_FP64: return launch_stage_fp64(stage, tx, ty, nb, smem, st, g, a);
-    case P_MIXED: return launch_stage_mixed(stage, tx, ty, nb, smem, st, g, a);
-    default: return launch_stage_fp32(stage, tx, ty, nb, smem, st, g, a);
+    case P_FP64: return launch_stage_fp64(stage, tx, ty, nb, smem, st, g, a, maps);
+    case P_MIXED: return launch_stage_mixed(stage, tx, ty, nb, smem, st, g, a, maps);
+    default: return launch_stage_fp32(stage, tx, ty, nb, smem, st, g, a, maps);
   }
 }
 cudaError_t launch_prims(int prec, unsigned nb, cudaStream_t st, const Geo& g, const StageArgs& a) {
@@ -125,14 +134,26 @@ size_t stage_smem_bytes(int prec, int tx, int ty) {
 bool stage_tile_supported(int prec, int tx, int ty) { return stage_smem_bytes(prec, tx, ty) > 0; }
 
 // Dynamic shared memory of the kernels a configuration launches: the
-// characteristic-reconstruction kernels also hold per-cell slopes.
-static size_t config_smem_bytes(int prec, int recon, int tx, int ty) {
+// characteristic-reconstruction kernels also hold per-cell slopes, the
+// learned switch its face queue (and both keep the unpadded ring).
+static size_t config_smem_bytes(int prec, int recon, int riemann, int tx, int ty) {
   if (recon == MHD_RECON_CHARACTERISTIC) {
     switch (prec) {
       case P_FP64: return smem_bytes_char_fp64();
       case P_MIXED: return smem_bytes_char_mixed();
       default: return smem_bytes_char_fp32();
     }
+  }
+  if (riemann == MHD_LEARNED) {
+    // the learned kernel and the plain one (the rhs and dump paths) share the handle's size
+    size_t l;
+    switch (prec) {
+      case P_FP64: l = smem_bytes_learned_fp64(); break;
+      case P_MIXED: l = smem_bytes_learned_mixed(); break;
+      default: l = smem_bytes_learned_fp32(); break;
+    }
+    const size_t p = stage_smem_bytes(prec, tx, ty);
+    return l > p ? l : p;
   }
   return stage_smem_bytes(prec, tx, ty);
 }
@@ -180,6 +201,10 @@ struct mhd_handle {
   cudaEvent_t ev_h2d[kSlots] = {}, ev_comp[kSlots] = {}, ev_d2h[kSlots] = {};
   long long nstream = 0;                   // streamed steps since the handle was created
   unsigned long long floors_seen = 0;      // floor hits already reported (MHD_FLOOR_ERROR)
+  // TMA maps of the two primitive buffers (plain kernels with 4-byte
+  // primitives); the W pointers swap every step, so each map keeps its base
+  TmaMaps tmaps[2] = {};
+  void* tmap_base[2] = {nullptr, nullptr};
 };
 
 // error text of calls without a handle, one per host thread (calls on
@@ -260,6 +285,8 @@ static int validate(const mhd_config* c, mhd_handle* h) {
   if (c->integrator != MHD_RK2 && c->integrator != MHD_RK3) return fail(h, MHD_ERR_INVALID, "unknown integrator");
   if (c->floor_policy != MHD_FLOOR_COUNT && c->floor_policy != MHD_FLOOR_ERROR)
     return fail(h, MHD_ERR_INVALID, "unknown floor policy");
+  if (c->plane_copy != MHD_COPY_AUTO && c->plane_copy != MHD_COPY_GATHER)
+    return fail(h, MHD_ERR_INVALID, "unknown plane copy mode");
   if (c->integrator == MHD_RK3 && (tx != 16 || ty != 8))
     return fail(h, MHD_ERR_INVALID, "SSP-RK3 is instantiated for the 16x8 tile only (got %dx%d)", tx, ty);
   if (c->integrator == MHD_RK3 && c->riemann == MHD_LEARNED)
@@ -269,9 +296,9 @@ static int validate(const mhd_config* c, mhd_handle* h) {
   if (c->recon == MHD_RECON_CHARACTERISTIC &&
       (tx != 16 || ty != 8 || c->integrator != MHD_RK2 || c->riemann == MHD_LEARNED))
     return fail(h, MHD_ERR_INVALID, "characteristic reconstruction runs on the 16x8 tile with RK2 and HLLD or HLL");
-  if (config_smem_bytes(c->precision, c->recon, tx, ty) > 227 * 1024)
+  if (config_smem_bytes(c->precision, c->recon, c->riemann, tx, ty) > 227 * 1024)
     return fail(h, MHD_ERR_INVALID, "tile %dx%d needs %zu B of shared memory (> 227 KB)", tx, ty,
-                config_smem_bytes(c->precision, c->recon, tx, ty));
+                config_smem_bytes(c->precision, c->recon, c->riemann, tx, ty));
   return MHD_OK;
 }
 
@@ -311,6 +338,60 @@ static void fill_geo(const mhd_config* c, Geo* g) {
   g->total = o;
 }
 
+// ---- TMA maps -----------------------------------------------------------------
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    cudaGetLastError();
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+
+// Maps of one primitive buffer: 4D (x, y, z, array) over 11 arrays of n0 x
+// n1 x n2 floats; the 8-primitive plane box and the 3-field lower-face box
+// of a tile's ring (ring x-offset 4).  Left off (on = 0) where the form has
+// no TMA path or the layout breaks a tensor-copy rule (rows of n0 floats
+// must be multiples of 16 bytes).
+static void build_tma_maps(const mhd_handle* h, void* wbuf, TmaMaps* out) {
+  memset(out, 0, sizeof *out);
+  const Geo& g = h->geo;
+  const mhd_config& c = h->cfg;
+  if (c.plane_copy != MHD_COPY_AUTO || c.precision == MHD_FP64 || c.recon != MHD_RECON_PRIMITIVE ||
+      c.riemann == MHD_LEARNED)
+    return;
+  if (g.n[2] < 2 || g.n[0] % 4 != 0 || ((uintptr_t)wbuf & 15u)) return;
+  const EncodeTiledFn encode = tensor_map_encoder();
+  if (!encode) return;
+  const cuuint32_t W = (cuuint32_t)(g.TX + 8), H = (cuuint32_t)(g.TY + 4);
+  const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], (cuuint64_t)NW};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4, (cuuint64_t)g.ncell * 4};
+  const cuuint32_t box_p[4] = {W, H, 1, 8}, box_b[4] = {W, H - 2, 1, 3}, es[4] = {1, 1, 1, 1};
+  const CUresult r1 = encode(reinterpret_cast<CUtensorMap*>(&out->p), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, wbuf, dims,
+                             strides, box_p, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r2 = encode(reinterpret_cast<CUtensorMap*>(&out->bn), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, wbuf, dims,
+                             strides, box_b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  out->on = r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+}
+
+// the maps of the buffer a stage reads its primitives from, or null
+static const TmaMaps* tma_for(const mhd_handle* h, const void* win) {
+  for (int i = 0; i < 2; ++i)
+    if (h->tmaps[i].on && h->tmap_base[i] == win) return &h->tmaps[i];
+  return nullptr;
+}
+
 static long long face_count(const Geo& g, int d) {
   long long n[3] = {g.n[0], g.n[1], g.n[2]};
   n[d] = g.nf[d];
@@ -329,7 +410,7 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   h->elem = cfg->precision == MHD_FP32 ? 4 : 8;
   h->kelem = cfg->precision == MHD_FP64 ? 8 : 4;
   h->welem = cfg->precision == MHD_FP64 ? 8 : 4;
-  h->smem_bytes = config_smem_bytes(cfg->precision, cfg->recon, h->geo.TX, h->geo.TY);
+  h->smem_bytes = config_smem_bytes(cfg->precision, cfg->recon, cfg->riemann, h->geo.TX, h->geo.TY);
   cudaError_t e = cudaGetDevice(&h->device);
   const size_t bytes = (size_t)h->geo.total * h->elem;
   const size_t kbytes = (size_t)h->geo.total * h->kelem;
@@ -354,6 +435,10 @@ extern "C" int mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_handle**
   }
   h->status = (unsigned int*)(h->words + 3);
   h->counters = h->words + 8;
+  for (int i = 0; i < 2; ++i) {
+    h->tmap_base[i] = h->W[i];
+    build_tma_maps(h, h->W[i], &h->tmaps[i]);
+  }
   e = cudaMemsetAsync(h->words, 0, 64 * sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->U[0], 0, bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->K1, 0, kbytes, h->stream);
@@ -497,7 +582,7 @@ static cudaError_t launch_step_rk3(mhd_handle* h, double dt) {
     a.Win = win[s];
     a.Wout = wout[s];
     if (h->profiling && (e = record_event(h))) return e;
-    e = launch_stage(prec, ST_RK3_1 + s, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a);
+    e = launch_stage(prec, ST_RK3_1 + s, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a, tma_for(h, a.Win));
     if (e) return e;
   }
   if (h->profiling && (e = record_event(h))) return e;
@@ -522,7 +607,7 @@ static cudaError_t launch_step(mhd_handle* h, double dt) {
   a.K1out = h->K1;
   a.Wout = h->W[h->cur ^ 1];
   if (h->profiling && (e = record_event(h))) return e;
-  e = launch_stage(prec, 1, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a);
+  e = launch_stage(prec, 1, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a, tma_for(h, a.Win));
   if (e) return e;
   if (h->profiling && (e = record_event(h))) return e;
   a.K1 = h->K1;
@@ -530,7 +615,7 @@ static cudaError_t launch_step(mhd_handle* h, double dt) {
   a.Win = h->W[h->cur ^ 1];
   a.Wout = h->W[h->cur];     // W(U^n) is dead once stage 1 has read it
   a.Uout = h->U[h->cur ^ 1];
-  e = launch_stage(prec, 2, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a);
+  e = launch_stage(prec, 2, g.TX, g.TY, nblocks, h->smem_bytes, h->stream, g, a, tma_for(h, a.Win));
   if (e) return e;
   if (h->profiling && (e = record_event(h))) return e;
   // U^{n+1} is in U[cur^1] and its primitives in W[cur]: swap the W buffers
@@ -571,7 +656,7 @@ static int check_status(mhd_handle* h) {
   if (rc) return rc;
   unsigned st = *(unsigned*)((unsigned long long*)h->pinned + 3);
   if (st & ST_NONFINITE) return fail(h, MHD_ERR_NONFINITE, "non-finite state value met on the device");
-  if (st & ST_TIMEOUT) return fail(h, MHD_ERR_TIMEOUT, "device barrier timed out");
+  if (st & ST_TIMEOUT) return fail(h, MHD_ERR_TIMEOUT, "a device wait timed out (barrier or plane copy)");
   if (h->cfg.floor_policy == MHD_FLOOR_ERROR) {
     const unsigned long long* hp = (const unsigned long long*)h->pinned;
     unsigned long long hits = hp[8 + C_RHO_FLOOR] + hp[8 + C_P_FLOOR];
@@ -736,7 +821,7 @@ extern "C" int mhd_rhs(mhd_handle* h, void* cell[5], void* face[3], int on_devic
   a.K1out = h->K1;
   a.Wout = nullptr;                         // no primitives of U + dt L
   e = launch_stage(h->cfg.precision, 1, g.TX, g.TY, (unsigned)(g.ntx * g.nty * g.nchunk), h->smem_bytes,
-                   h->stream, g, a);
+                   h->stream, g, a, tma_for(h, a.Win));
   if (e) return fail(h, MHD_ERR_CUDA, "stage launch failed: %s", cudaGetErrorString(e));
   int rc = copy_arrays(h, false, (char*)h->K1, h->kelem, cell, face, on_device);
   if (rc) return rc;
@@ -882,6 +967,7 @@ extern "C" int mhd_get_stats(mhd_handle* h, mhd_stats* out) {
   out->faces_hlld = (long long)hp[8 + C_HLLD];
   out->last_dt = h->last_dt;
   out->steps = h->steps;
+  out->tma_planes = (long long)hp[8 + C_TMA];
   return MHD_OK;
 }
 

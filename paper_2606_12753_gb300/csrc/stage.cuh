@@ -39,7 +39,7 @@ template <class A, class B> struct Pick<false, A, B> { using type = B; };
 // status bits
 enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 // counters
-enum { C_RHO_FLOOR = 0, C_P_FLOOR = 1, C_HLL = 2, C_HLLD = 3, C_NCOUNT = 8 };
+enum { C_RHO_FLOOR = 0, C_P_FLOOR = 1, C_HLL = 2, C_HLLD = 3, C_TMA = 4, C_NCOUNT = 8 };
 // number of primitive arrays
 enum { NW = 11 };
 
@@ -232,9 +232,25 @@ __device__ __forceinline__ R cfl_speed(const Geo& g, const R* w) {
   return sum;
 }
 
-// launchers defined next to the kernels (one translation unit per precision)
+// Tensor maps of one primitive array set W (11 arrays of n0 x n1 x n2, 4-byte
+// elements), built on the host with the driver's tensor-map encoder: the
+// plane box of the 8 ring primitives (W x H x 1 x 8, at x = tile origin - 4,
+// y = tile origin - 2) and of the 3 lower-face fields (W x (TY+2) x 1 x 3, at
+// y = tile origin - 1, array 8).  on = 0: no TMA (every plane by the
+// per-element gather).  Passed to the kernel as a __grid_constant__
+// parameter, so the TMA instructions can name the maps in parameter space.
+struct alignas(64) TmaDesc {
+  unsigned long long opaque[16];
+};
+struct TmaMaps {
+  TmaDesc p, bn;
+  int on;
+};
+
+// launchers defined next to the kernels (one translation unit per precision);
+// tm: tensor maps of a.Win for the plain stage kernels, or null (no TMA)
 cudaError_t launch_stage(int prec, int stage, int tx, int ty, unsigned nblocks, size_t smem, cudaStream_t st,
-                         const Geo& g, const StageArgs& a);
+                         const Geo& g, const StageArgs& a, const TmaMaps* tm = nullptr);
 cudaError_t launch_prims(int prec, unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& a);
 cudaError_t stage_set_smem(int prec, int tx, int ty, size_t bytes);
 size_t stage_smem_bytes(int prec, int tx, int ty);

@@ -1,115 +1,5 @@
 // Stage-kernel instantiations and launchers for the fp64 form.
-#include "stage_impl.cuh"
-
-namespace mhd {
-
+#define MHD_UNIT_PREC P_FP64
+#define MHD_UNIT_FN(name) name##_fp64
 #define MHD_TILES(X) X(16, 8) X(24, 8) X(8, 8)
-
-cudaError_t launch_stage_fp64(int stage, int tx, int ty, unsigned nblocks, size_t smem, cudaStream_t st,
-                                 const Geo& g, const StageArgs& args) {
-#define X(TXv, TYv)                                                                              \
-  if (tx == TXv && ty == TYv) {                                                                  \
-    if (stage == 1) stage_kernel<P_FP64, 1, TXv, TYv><<<nblocks, stage_threads<P_FP64, TXv, TYv>(), smem, st>>>(g, args);     \
-    else stage_kernel<P_FP64, 2, TXv, TYv><<<nblocks, stage_threads<P_FP64, TXv, TYv>(), smem, st>>>(g, args);                \
-    return cudaGetLastError();                                                                   \
-  }
-  MHD_TILES(X)
-#undef X
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t set_smem_fp64(int tx, int ty, size_t bytes) {
-#define X(TXv, TYv)                                                                                        \
-  if (tx == TXv && ty == TYv) {                                                                            \
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<P_FP64, 1, TXv, TYv>,                              \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);         \
-    if (e == cudaSuccess)                                                                                  \
-      e = cudaFuncSetAttribute(stage_kernel<P_FP64, 2, TXv, TYv>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                               (int)bytes);                                                                \
-    return e;                                                                                              \
-  }
-  MHD_TILES(X)
-#undef X
-  return cudaErrorInvalidValue;
-}
-
-size_t smem_bytes_fp64(int tx, int ty) {
-  using R = Prec<P_FP64>::R;
-  using S = Prec<P_FP64>::S;
-#define X(TXv, TYv) \
-  if (tx == TXv && ty == TYv) return Tile<TXv, TYv>::bytes<R, S, slopes_in_smem<P_FP64, FM_PLAIN, TXv, TYv>()>();
-  MHD_TILES(X)
-#undef X
-  return 0;
-}
-
-// characteristic reconstruction (16 x 8 tile) keeps its slopes in shared memory
-size_t smem_bytes_char_fp64() { return Tile<16, 8>::bytes<Prec<P_FP64>::R, Prec<P_FP64>::S, true>(); }
-
-cudaError_t launch_prims_fp64(unsigned nblocks, cudaStream_t st, const Geo& g, const StageArgs& args) {
-  (void)nblocks;   // one CTA per (j, k) row of cells
-  prims_kernel<P_FP64><<<(unsigned)((long long)g.n[1] * g.n[2]), 128, 0, st>>>(g, args);
-  return cudaGetLastError();
-}
-
-// The learned HLL/HLLD switch is instantiated for the 16 x 8 tile only.
-cudaError_t launch_stage_learned_fp64(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
-                                   const StageArgs& args) {
-  if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
-  if (stage == 1) stage_kernel_learned<P_FP64, 1, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
-  else stage_kernel_learned<P_FP64, 2, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
-  return cudaGetLastError();
-}
-
-cudaError_t set_smem_learned_fp64(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel_learned<P_FP64, 1, 16, 8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage_kernel_learned<P_FP64, 2, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-  return e;
-}
-
-// SSP-RK3 stages (ids 3, 4, 5) are instantiated for the 16 x 8 tile only.
-cudaError_t launch_stage_rk3_fp64(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
-                                const StageArgs& args) {
-  if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
-  if (stage == ST_RK3_1) stage_kernel<P_FP64, ST_RK3_1, 16, 8><<<nblocks, stage_threads<P_FP64, 16, 8>(), smem, st>>>(g, args);
-  else if (stage == ST_RK3_2) stage_kernel<P_FP64, ST_RK3_2, 16, 8><<<nblocks, stage_threads<P_FP64, 16, 8>(), smem, st>>>(g, args);
-  else if (stage == ST_RK3_3) stage_kernel<P_FP64, ST_RK3_3, 16, 8><<<nblocks, stage_threads<P_FP64, 16, 8>(), smem, st>>>(g, args);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
-cudaError_t set_smem_rk3_fp64(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<P_FP64, ST_RK3_1, 16, 8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage_kernel<P_FP64, ST_RK3_2, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage_kernel<P_FP64, ST_RK3_3, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-  return e;
-}
-
-// Characteristic reconstruction (RK2 stages, 16 x 8 tile).
-cudaError_t launch_stage_char_fp64(int stage, unsigned nblocks, size_t smem, cudaStream_t st, const Geo& g,
-                                 const StageArgs& args) {
-  if (g.TX != 16 || g.TY != 8) return cudaErrorInvalidValue;
-  if (stage == 1) stage_kernel_char<P_FP64, 1, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
-  else if (stage == 2) stage_kernel_char<P_FP64, 2, 16, 8><<<nblocks, 256, smem, st>>>(g, args);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
-cudaError_t set_smem_char_fp64(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel_char<P_FP64, 1, 16, 8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage_kernel_char<P_FP64, 2, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-  return e;
-}
-
-}  // namespace mhd
+#include "stage_unit.cuh"

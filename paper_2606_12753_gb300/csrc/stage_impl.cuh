@@ -29,10 +29,19 @@
 
 namespace mhd {
 
-template <int TX, int TY>
+// XO: ring column of the tile's first cell.  2 holds exactly the 2-cell
+// halo; 4 makes a ring row start 4 cells left of the tile, so that a plane
+// of 4-byte primitives can arrive as one TMA box whose first column (x =
+// tile origin - 4, a multiple of 4) meets the 16-byte rule of tensor copies.
+template <int TX, int TY, int XO = 2>
 struct Tile {
-  static constexpr int W = TX + 4, H = TY + 4;
+  static constexpr int XOFF = XO;
+  static constexpr int W = TX + 2 * XO, H = TY + 4;
   static constexpr int nR = W * H;
+  // lower-face normal fields of a plane: rows -1..TY of the ring (the rows
+  // any face reads), 3 arrays; a plane's slot padded to 128 bytes
+  static constexpr int nB = W * (TY + 2);
+  static constexpr int nBslot = (3 * nB + 31) / 32 * 32;
   static constexpr int nX = (TX + 1) * (TY + 2);
   static constexpr int nY = (TX + 2) * (TY + 1);
   static constexpr int nZ = (TX + 2) * (TY + 2);
@@ -41,7 +50,7 @@ struct Tile {
   // offsets in units of R
   static constexpr int oP = 0;
   static constexpr int oBN = oP + 4 * 8 * nR;
-  static constexpr int oHX = oBN + 2 * 3 * nR;
+  static constexpr int oHX = oBN + 2 * nBslot;
   static constexpr int oHY = oHX + 5 * nX;
   static constexpr int oHZ = oHY + 5 * nY;
   static constexpr int oXC = oHZ + 5 * nZ;
@@ -58,22 +67,30 @@ struct Tile {
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
   static constexpr int nI = W + H + 6;   // column/row maps, switch counters, the stage's dt
+  // then four mbarriers (8 bytes each), one per ring slot, for TMA planes
   // per-cell half slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
   // x and y slopes of the current plane, z slopes of two planes (by parity)
   static constexpr int nSl = 7 * nZ;
   static constexpr int nSlope = 4 * nSl;
-  template <typename R, typename S>
-  __host__ __device__ static constexpr size_t core_bytes() {
-    size_t b = (size_t)nRtot * sizeof(R);
-    b = (b + 15) / 16 * 16;
-    b += (size_t)nItems * sizeof(unsigned short);
-    b = (b + 15) / 16 * 16;
-    b += (size_t)nI * sizeof(int);
-    return (b + 15) / 16 * 16;
+  // byte offsets of the regions after the R arrays: the learned switch's
+  // queue (QUEUE only), the int tables, the mbarriers
+  template <typename R, bool QUEUE>
+  __host__ __device__ static constexpr size_t queue_off() { return ((size_t)nRtot * sizeof(R) + 15) / 16 * 16; }
+  template <typename R, bool QUEUE>
+  __host__ __device__ static constexpr size_t int_off() {
+    return (queue_off<R, QUEUE>() + (QUEUE ? (size_t)nItems * sizeof(unsigned short) : 0) + 15) / 16 * 16;
   }
-  template <typename R, typename S, bool SLOPES = false>
+  template <typename R, bool QUEUE>
+  __host__ __device__ static constexpr size_t mbar_off() {
+    return (int_off<R, QUEUE>() + (size_t)nI * sizeof(int) + 15) / 16 * 16;
+  }
+  template <typename R, typename S, bool QUEUE = false>
+  __host__ __device__ static constexpr size_t core_bytes() {
+    return (mbar_off<R, QUEUE>() + 4 * sizeof(unsigned long long) + 15) / 16 * 16;
+  }
+  template <typename R, typename S, bool SLOPES = false, bool QUEUE = false>
   static constexpr size_t bytes() {
-    return core_bytes<R, S>() + (SLOPES ? (size_t)nSlope * sizeof(R) : 0);
+    return core_bytes<R, S, QUEUE>() + (SLOPES ? (size_t)nSlope * sizeof(R) : 0);
   }
 };
 
@@ -147,6 +164,13 @@ constexpr bool slopes_in_smem() {
   return MODE == FM_CHAR || (PREC == P_FP64 && MODE == FM_PLAIN && TX * TY <= 128);
 }
 
+// Ring x-offset of a kernel: the plain kernels with 4-byte primitives (mixed,
+// FP32) pad the ring rows so that interior planes can arrive by TMA.
+template <int PREC, int MODE>
+__host__ __device__ constexpr int ring_xo() {
+  return PREC != P_FP64 && MODE == FM_PLAIN ? 4 : 2;
+}
+
 // SPLIT: the update phase splits each cell between two threads (face group
 // and conserved group, named-barrier hand-over); the CTA then needs at least
 // two threads per cell of a plane.  Measured faster for the mixed and FP64
@@ -161,8 +185,17 @@ struct StageKernel {
   using R = typename Prec<PREC>::R;
   using S = typename Prec<PREC>::S;
   using K = typename Prec<PREC>::K;
-  using T = Tile<TX, TY>;
+  using T = Tile<TX, TY, ring_xo<PREC, MODE>()>;
   static constexpr int W = T::W;
+  static constexpr int XO = T::XOFF;
+  // TMA planes: plain kernels with 4-byte primitives
+  static constexpr bool kTMA = MODE == FM_PLAIN && PREC != P_FP64;
+  static_assert(!kTMA || ((8 * T::nR * sizeof(R)) % 128 == 0 && (T::oBN * sizeof(R)) % 128 == 0 &&
+                          (T::nBslot * sizeof(R)) % 128 == 0 && (T::W * sizeof(R)) % 16 == 0),
+                "TMA ring slots must start on 128-byte boundaries and rows span whole 16-byte units");
+  // lower-face arrays of plane q, and the index in them of ring cell r
+  static __device__ __forceinline__ const R* bn_slot(const R* sm, int q) { return sm + T::oBN + (q & 1) * T::nBslot; }
+  static __device__ __forceinline__ int bn_of(int r) { return r - W; }
 
   // ---------------------------------------------------------------- phase A
   // Threads [t0, blockDim.x) load, item r = threadIdx.x - t0 with stride
@@ -171,7 +204,7 @@ struct StageKernel {
                                                     const int* rowc, double dt, int gi0, int gj0, int m,
                                                     bool write_bn, int t0 = 0) {
     R* P = sm + T::oP + (m & 3) * 8 * T::nR;
-    R* BN = sm + T::oBN + (m & 1) * 3 * T::nR;
+    R* BN = sm + T::oBN + (m & 1) * T::nBslot;
     const bool zin = g.bc[2] == 0 || (m >= 0 && m < g.n[2]);
     const int ck = wrapc(m, g.n[2], g.bc[2]);
     const R* Win = (const R*)a.Win;
@@ -179,7 +212,7 @@ struct StageKernel {
     if (t < 0) return;
     for (int r = t; r < T::nR; r += (int)blockDim.x - t0) {
       const int x = r % W, y = r / W;
-      const int gi = gi0 - 2 + x, gj = gj0 - 2 + y;
+      const int gi = gi0 - XO + x, gj = gj0 - 2 + y;
       const bool inside = zin && (g.bc[0] == 0 || (gi >= 0 && gi < g.n[0])) &&
                           (g.bc[1] == 0 || (gj >= 0 && gj < g.n[1]));
       R w[NW];
@@ -204,11 +237,77 @@ struct StageKernel {
       }
 #pragma unroll
       for (int v = 0; v < 8; ++v) P[v * T::nR + r] = w[v];
-      if (write_bn) {
+      if (write_bn && y >= 1 && y <= TY + 2) {   // the lower-face rows -1..TY
 #pragma unroll
-        for (int d = 0; d < 3; ++d) BN[d * T::nR + r] = w[8 + d];
+        for (int d = 0; d < 3; ++d) BN[d * T::nB + bn_of(r)] = w[8 + d];
       }
     }
+  }
+
+  // ------------------------------------------------------- phase A by TMA
+  // A plane of an interior tile (its ring needs no periodic wrap and no
+  // outflow ghost) arrives as two TMA boxes, issued by one thread: the 8
+  // primitives into the plane's ring slot, the 3 lower-face fields into its
+  // lower-face slot (when the plane needs them).  Both complete on the ring
+  // slot's mbarrier; every thread waits on it before the flux phase that
+  // reads the plane.  The slot was last read (generic proxy) before the
+  // barrier that precedes the issue, so one proxy fence orders those reads
+  // before the asynchronous writes.
+  static __device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+  }
+  static __device__ __forceinline__ void tma_init(unsigned long long* mbar) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + s)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  static __device__ __forceinline__ void tma_issue(const TmaMaps& tm, R* sm, unsigned long long* mbar, int m, int ck,
+                                                   int gi0, int gj0, bool with_bn) {
+    const unsigned bar = smem_u32(mbar + (m & 3));
+    const unsigned bytes = (unsigned)((8 * T::nR + (with_bn ? 3 * T::nB : 0)) * sizeof(R));
+    unsigned long long state;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(state) : "r"(bar), "r"(bytes) : "memory");
+    (void)state;
+    const unsigned dp = smem_u32(sm + T::oP + (m & 3) * 8 * T::nR);
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dp), "l"(&tm.p), "r"(gi0 - XO), "r"(gj0 - 2), "r"(ck), "r"(0), "r"(bar)
+        : "memory");
+    if (with_bn) {
+      const unsigned db = smem_u32(sm + T::oBN + (m & 1) * T::nBslot);
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+          "[%6];" ::"r"(db), "l"(&tm.bn), "r"(gi0 - XO), "r"(gj0 - 1), "r"(ck), "r"(8), "r"(bar)
+          : "memory");
+    }
+  }
+  // Wait for the TMA plane of ring slot s; phases: one parity bit per slot,
+  // flipped by every completed load of that slot.  A wait that outlasts 1 s
+  // raises the timeout bit of the status word and lets the CTA go on (the
+  // host reports MHD_ERR_TIMEOUT; nothing hangs).
+  static __device__ __forceinline__ void tma_wait(const StageArgs& a, unsigned long long* mbar, int s,
+                                                  unsigned& phases) {
+    const unsigned bar = smem_u32(mbar + s);
+    const unsigned par = (phases >> s) & 1u;
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+      unsigned done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done) : "r"(bar), "r"(par) : "memory");
+      if (done) break;
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (it == 0) t0 = now;
+      else if (now - t0 > 1000000000ull) {
+        atomicOr(a.status, (unsigned)ST_TIMEOUT);
+        break;
+      }
+    }
+    phases ^= 1u << s;
   }
 
   // ---------------------------------------------------------------- phase B
@@ -254,7 +353,7 @@ struct StageKernel {
     for (int it = first + threadIdx.x; it < 3 * n; it += blockDim.x) {
       const int D = it / n, cidx = it - D * n;
       const int i = cidx % (TX + 2) - 1, j = cidx / (TX + 2) - 1;
-      const int r = (i + 2) + W * (j + 2);
+      const int r = (i + XO) + W * (j + 2);
       R c[3][7], out[7];
       R bnc = R(0);
       if (D == 0) {
@@ -290,7 +389,7 @@ struct StageKernel {
     const R gam = gpar<R>(g.gamma, g.fgamma);
     const R ig = R(1) / (gam - R(1));
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
-    const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
+    const R* BNq = bn_slot(sm, q);
     constexpr int n = T::nZ;
     for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
       R c1[7], c2[7], s1[7], s2[7], wl[7], wr[7], f[7], bn, cm;
@@ -299,10 +398,10 @@ struct StageKernel {
       const R* sb;
       if (w < nZ) {
         const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
-        const int r = (i + 2) + W * (j + 2);
+        const int r = (i + XO) + W * (j + 2);
         gather<2>(sm + T::oP + (k & 3) * 8 * T::nR, T::nR, r, c1);
         gather<2>(sm + T::oP + ((k + 1) & 3) * 8 * T::nR, T::nR, r, c2);
-        bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
+        bn = bn_slot(sm, k + 1)[2 * T::nB + bn_of(r)];
         ia = ib = w;
         sa = sl + (2 + (k & 1)) * T::nSl;
         sb = sl + (2 + ((k + 1) & 1)) * T::nSl;
@@ -311,10 +410,10 @@ struct StageKernel {
       } else if (w < nZ + T::nX) {
         o = w - nZ;
         const int i = o % (TX + 1), j = o / (TX + 1) - 1;
-        const int r = (i + 2) + W * (j + 2);
+        const int r = (i + XO) + W * (j + 2);
         gather<0>(Pq, T::nR, r - 1, c1);
         gather<0>(Pq, T::nR, r, c2);
-        bn = BNq[r];
+        bn = BNq[bn_of(r)];
         ia = i + (TX + 2) * (j + 1);
         ib = ia + 1;
         sa = sb = sl;
@@ -322,10 +421,10 @@ struct StageKernel {
       } else {
         o = w - nZ - T::nX;
         const int i = o % (TX + 2) - 1, j = o / (TX + 2);
-        const int r = (i + 2) + W * (j + 2);
+        const int r = (i + XO) + W * (j + 2);
         gather<1>(Pq, T::nR, r - W, c1);
         gather<1>(Pq, T::nR, r, c2);
-        bn = BNq[T::nR + r];
+        bn = BNq[T::nB + bn_of(r)];
         ib = (i + 1) + (TX + 2) * (j + 1);
         ia = ib - (TX + 2);
         sa = sb = sl + T::nSl;
@@ -355,7 +454,7 @@ struct StageKernel {
     R* EC = sm + T::oEC + (q & 1) * 3 * T::nZ;
     for (int w = threadIdx.x; w < T::nZ; w += blockDim.x) {
       const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
-      const int r = (i + 2) + W * (j + 2);
+      const int r = (i + XO) + W * (j + 2);
       const R vx = Pq[1 * T::nR + r], vy = Pq[2 * T::nR + r], vz = Pq[3 * T::nR + r];
       const R bx = Pq[5 * T::nR + r], by = Pq[6 * T::nR + r], bz = Pq[7 * T::nR + r];
       EC[w] = vz * by - vy * bz;
@@ -374,13 +473,13 @@ struct StageKernel {
   static __device__ __forceinline__ int item_stencil(const R* sm, int k, int q, int nZ, int w, R (&c)[4][7], R& bn,
                                                      int& o, R* bnc = nullptr) {
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
-    const R* BNq = sm + T::oBN + (q & 1) * 3 * T::nR;
+    const R* BNq = bn_slot(sm, q);
     if (w < nZ) {
       const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
-      const int r = (i + 2) + W * (j + 2);
+      const int r = (i + XO) + W * (j + 2);
 #pragma unroll
       for (int s = 0; s < 4; ++s) gather<2>(sm + T::oP + ((k - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
-      bn = sm[T::oBN + ((k + 1) & 1) * 3 * T::nR + 2 * T::nR + r];
+      bn = bn_slot(sm, k + 1)[2 * T::nB + bn_of(r)];
       if (bnc) {
         bnc[0] = sm[T::oP + (k & 3) * 8 * T::nR + 7 * T::nR + r];
         bnc[1] = sm[T::oP + ((k + 1) & 3) * 8 * T::nR + 7 * T::nR + r];
@@ -391,10 +490,10 @@ struct StageKernel {
     if (w < nZ + T::nX) {
       o = w - nZ;
       const int i = o % (TX + 1), j = o / (TX + 1) - 1;
-      const int r = (i + 2) + W * (j + 2);
+      const int r = (i + XO) + W * (j + 2);
 #pragma unroll
       for (int s = 0; s < 4; ++s) gather<0>(Pq, T::nR, r - 2 + s, c[s]);
-      bn = BNq[r];
+      bn = BNq[bn_of(r)];
       if (bnc) {
         bnc[0] = Pq[5 * T::nR + r - 1];
         bnc[1] = Pq[5 * T::nR + r];
@@ -403,10 +502,10 @@ struct StageKernel {
     }
     o = w - nZ - T::nX;
     const int i = o % (TX + 2) - 1, j = o / (TX + 2);
-    const int r = (i + 2) + W * (j + 2);
+    const int r = (i + XO) + W * (j + 2);
 #pragma unroll
     for (int s = 0; s < 4; ++s) gather<1>(Pq, T::nR, r + (s - 2) * W, c[s]);
-    bn = BNq[T::nR + r];
+    bn = BNq[T::nB + bn_of(r)];
     if (bnc) {
       bnc[0] = Pq[6 * T::nR + r - W];
       bnc[1] = Pq[6 * T::nR + r];
@@ -953,16 +1052,18 @@ struct StageKernel {
 
   // One work item: tile `item` (x fastest, then y, then z chunk) of one box.
   // Shared memory is the caller's dynamic allocation; every thread of the
-  // CTA calls this with the same arguments.
-  static __device__ void run_item(const Geo& g, const StageArgs& a, int item, unsigned char* smem_raw) {
+  // CTA calls this with the same arguments.  tm: tensor maps of the stage's
+  // input primitives (plain kernels with 4-byte primitives), or null.
+  static __device__ void run_item(const Geo& g, const StageArgs& a, int item, unsigned char* smem_raw,
+                                  const TmaMaps* tm = nullptr) {
     R* sm = reinterpret_cast<R*>(smem_raw);
-    constexpr size_t qOff = ((size_t)T::nRtot * sizeof(R) + 15) / 16 * 16;
-    unsigned short* queue = reinterpret_cast<unsigned short*>(smem_raw + qOff);   // learned switch only
-    constexpr size_t iOff = ((qOff + (size_t)T::nItems * sizeof(unsigned short)) + 15) / 16 * 16;
-    int* colc = reinterpret_cast<int*>(smem_raw + iOff);
+    unsigned short* queue =
+        reinterpret_cast<unsigned short*>(smem_raw + T::template queue_off<R, LEARN>());   // learned switch only
+    int* colc = reinterpret_cast<int*>(smem_raw + T::template int_off<R, LEARN>());
     int* rowc = colc + W;
     int* qcnt = rowc + T::H;
-    constexpr size_t sl_off = T::template core_bytes<R, S>();
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw + T::template mbar_off<R, LEARN>());
+    constexpr size_t sl_off = T::template core_bytes<R, S, LEARN>();
     R* sl = reinterpret_cast<R*>(smem_raw + sl_off);   // used when SLOPES
 
     int b = item;
@@ -977,7 +1078,7 @@ struct StageKernel {
     if (StageTraits<STAGE>::first && item == 0 && threadIdx.x == 0) *a.nextword = 0ull;
     __syncthreads();   // the previous item of this CTA may still read the tables
     for (int t = threadIdx.x; t < T::W + T::H; t += blockDim.x) {
-      if (t < T::W) colc[t] = wrapc(gi0 - 2 + t, g.n[0], g.bc[0]);
+      if (t < T::W) colc[t] = wrapc(gi0 - XO + t, g.n[0], g.bc[0]);
       else rowc[t - T::W] = wrapc(gj0 - 2 + (t - T::W), g.n[1], g.bc[1]);
     }
     if (LEARN && threadIdx.x < 4) qcnt[threadIdx.x] = 0;
@@ -1026,10 +1127,31 @@ struct StageKernel {
       finish(a, nrho, np, nh, nd, bad, smax);
       return;
     }
-    load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 2, false);
-    load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb - 1, true);
-    load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, kb, true);
+    // TMA planes: every in-range plane of an interior tile (no periodic wrap,
+    // no outflow ghost across x or y); the rest by the per-element gather
+    bool tile_tma = false;
+    if constexpr (kTMA) {
+      // (and only if the ring slots sit on the 128-byte boundaries tensor
+      // copies write to: the slot sizes are multiples of 128 bytes)
+      tile_tma = tm != nullptr && tm->on != 0 && gi0 - 2 >= 0 && gi0 + TX + 1 < g.n[0] && gj0 - 2 >= 0 &&
+                 gj0 + TY + 1 < g.n[1] && (smem_u32(smem_raw) & 127u) == 0u;
+    }
+    const auto plane_tma = [&](int m) { return tile_tma && (g.bc[2] == 0 || (m >= 0 && m < g.n[2])); };
+    unsigned phases = 0, ntma = 0;   // ntma: planes thread 0 issued by TMA
+    if (tile_tma) tma_init(mbar);   // thread 0, before its first issue; others wait after a barrier
+    for (int m = kb - 2; m <= kb; ++m) {
+      if (plane_tma(m)) {
+        if (threadIdx.x == 0) {
+          tma_issue(*tm, sm, mbar, m, wrapc(m, g.n[2], g.bc[2]), gi0, gj0, m != kb - 2);
+          ++ntma;
+        }
+      } else {
+        load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, m, m != kb - 2);
+      }
+    }
     __syncthreads();
+    for (int m = kb - 2; m <= kb; ++m)
+      if (plane_tma(m)) tma_wait(a, mbar, m & 3, phases);
     if constexpr (SLOPES) {
       slopes(g, sm, sl, kb - 1, false);
       __syncthreads();
@@ -1040,12 +1162,20 @@ struct StageKernel {
       fluxes(g, sm, kb - 2, kb - 1, false);
     }
     __syncthreads();
+    // a TMA plane is issued as soon as the flux phase has freed its slot:
+    // plane k + 3 goes where plane k - 1 was, and lands during phases C, D
+    if (plane_tma(kb + 1) && threadIdx.x == 0) {
+      tma_issue(*tm, sm, mbar, kb + 1, wrapc(kb + 1, g.n[2], g.bc[2]), gi0, gj0, true);
+      ++ntma;
+    }
     ZCarry zc{S(0), R(0), false};   // face group: upper z-face of the previous plane
     for (int k = kb - 1; k < ke; ++k) {
       // the threads without a cell in the update phase load the next plane
-      // while the others finish that phase
-      load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true, T::nC < (int)blockDim.x ? T::nC : 0);
+      // while the others finish that phase (unless it comes by TMA)
+      const bool tma_next = plane_tma(k + 2);
+      if (!tma_next) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true, T::nC < (int)blockDim.x ? T::nC : 0);
       __syncthreads();
+      if (tma_next) tma_wait(a, mbar, (k + 2) & 3, phases);
       if constexpr (SLOPES) {
         slopes(g, sm, sl, k + 1, false);
         __syncthreads();
@@ -1056,6 +1186,10 @@ struct StageKernel {
         fluxes(g, sm, k, k + 1, true);
       }
       __syncthreads();
+      if (k + 3 <= ke + 1 && plane_tma(k + 3) && threadIdx.x == 0) {
+        tma_issue(*tm, sm, mbar, k + 3, wrapc(k + 3, g.n[2], g.bc[2]), gi0, gj0, true);
+        ++ntma;
+      }
       Pre pre;
       if constexpr (kPF) {
         if (k >= kb) prefetch(g, a, gi0, gj0, k, zc.have, pre);
@@ -1066,6 +1200,7 @@ struct StageKernel {
     }
 
     finish(a, nrho, np, nh, nd, bad, smax);
+    if (ntma && threadIdx.x == 0) atomicAdd(&a.counters[C_TMA], (unsigned long long)ntma);
   }
 };
 
@@ -1089,16 +1224,16 @@ __host__ __device__ constexpr bool stage_split() {
 
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_blocks<PREC, TX, TY>())
-    stage_kernel(Geo g, StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_kernel(Geo g, StageArgs a, const __grid_constant__ TmaMaps tm) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>(), PREC == P_FP64>::run_item(g, a, blockIdx.x,
-                                                                                                    smem_raw);
+                                                                                                    smem_raw, &tm);
 }
 
 // The same stage with the learned HLL/HLLD face switch.
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_learned(Geo g, StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY, FM_LEARNED, PREC != P_FP32 && 2 * TX * TY <= 256>::run_item(g, a, blockIdx.x,
                                                                                                smem_raw);
 }
@@ -1106,7 +1241,7 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_lear
 // The same stage with characteristic reconstruction.
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char(Geo g, StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   StageKernel<PREC, STAGE, TX, TY, FM_CHAR, PREC != P_FP32 && 2 * TX * TY <= 256, true>::run_item(g, a, blockIdx.x,
                                                                                                    smem_raw);
 }

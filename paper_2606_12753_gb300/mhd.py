@@ -19,6 +19,7 @@ from . import _build
 MHD_OK = 0
 MHD_ERR_INVALID, MHD_ERR_CUDA, MHD_ERR_NONFINITE, MHD_ERR_TIMEOUT, MHD_ERR_NOMEM, MHD_ERR_FLOOR = -1, -2, -3, -4, -5, -6
 MHD_FLOOR_COUNT, MHD_FLOOR_ERROR = 0, 1
+MHD_COPY_AUTO, MHD_COPY_GATHER = 0, 1
 MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
 MHD_FP64, MHD_MIXED, MHD_FP32 = 0, 1, 2
 MHD_HLLD, MHD_HLL, MHD_LEARNED = 0, 1, 2
@@ -40,13 +41,13 @@ class mhd_config(C.Structure):
                 ("precision", C.c_int), ("riemann", C.c_int), ("emf", C.c_int),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
-                ("integrator", C.c_int), ("recon", C.c_int), ("floor_policy", C.c_int)]
+                ("integrator", C.c_int), ("recon", C.c_int), ("floor_policy", C.c_int), ("plane_copy", C.c_int)]
 
 
 class mhd_stats(C.Structure):
     _fields_ = [("rho_floor_hits", C.c_longlong), ("p_floor_hits", C.c_longlong),
                 ("faces_hll", C.c_longlong), ("faces_hlld", C.c_longlong),
-                ("last_dt", C.c_double), ("status", C.c_int), ("steps", C.c_int)]
+                ("last_dt", C.c_double), ("status", C.c_int), ("steps", C.c_int), ("tma_planes", C.c_longlong)]
 
 
 class mhd_pipe_peaks(C.Structure):
@@ -291,7 +292,7 @@ class Solver:
 
     def __init__(self, box, precision="fp64", riemann="hlld", emf="upwind", tile=(0, 0, 0),
                  stream=None, cfl=None, rho_floor=1e-10, p_floor=1e-10, integrator="rk2", recon="primitive",
-                 floor_policy="count"):
+                 floor_policy="count", plane_copy="auto"):
         c = mhd_default_config(box.nx, box.ny, box.nz)
         c.dx, c.dy, c.dz = box.dx, box.dy, box.dz
         c.gamma = box.gamma
@@ -305,6 +306,7 @@ class Solver:
         c.integrator = INTEGRATORS[integrator] if isinstance(integrator, str) else integrator
         c.recon = RECONS[recon] if isinstance(recon, str) else recon
         c.floor_policy = {"count": MHD_FLOOR_COUNT, "error": MHD_FLOOR_ERROR}[floor_policy]
+        c.plane_copy = {"auto": MHD_COPY_AUTO, "gather": MHD_COPY_GATHER}[plane_copy]
         self.cfg = c
         self.dims = (box.nx, box.ny, box.nz)
         self.bc = tuple(box.bc)

@@ -42,7 +42,7 @@ def test_default_config_host_only():
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("gamma", 1.0), ("cfl", 0.0), ("precision", 7),
                                          ("riemann", 9), ("emf", 3), ("rho_floor", 0.0), ("tile_x", 65),
-                                         ("tile_y", -1), ("floor_policy", 2)])
+                                         ("tile_y", -1), ("floor_policy", 2), ("plane_copy", 5)])
 def test_invalid_config_rejected(field, value):
     c = mhd.mhd_default_config(16, 16, 16)
     setattr(c, field, value)
