@@ -61,6 +61,8 @@ extern "C" {
 #define MHD_ERR_TIMEOUT (-4)   /* a device-wide barrier gave up waiting */
 #define MHD_ERR_NOMEM (-5)     /* device allocation failed */
 #define MHD_ERR_FLOOR (-6)     /* a density or pressure floor was applied (only with MHD_FLOOR_ERROR) */
+#define MHD_ERR_BOUNDS (-7)    /* bounds-checked build only: a kernel index left its array (the access was
+                                  redirected to element 0; results are then invalid) */
 
 #define MHD_BC_PERIODIC 0
 #define MHD_BC_OUTFLOW 1

@@ -39,23 +39,38 @@ def _deps() -> list:
                   glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+# Build variants: the library, and its bounds-checked build (every kernel
+# index checked against its array; a violation sets a status bit instead of
+# touching memory), a separate in-tree library for small-case tests.
+VARIANTS = {"release": ([], "libmhd_gb300.so", "_build"),
+            "bounds": (["-DMHD_BOUNDS_CHECK"], "libmhd_gb300_bounds.so", "_build_bounds")}
+
+
+def variant_path(variant: str = "release") -> str:
+    return os.path.join(HERE, VARIANTS[variant][1])
+
+
+def needs_build(variant: str = "release") -> bool:
+    lib = variant_path(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, variant: str = "release") -> str:
+    vflags, libname, objdir = VARIANTS[variant]
+    lib_path = os.path.join(HERE, libname)
+    obj_dir = os.path.join(HERE, objdir)
+    if not force and not needs_build(variant):
+        return lib_path
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     cc = nvcc()
-    flags = NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + list(extra or [])
+    flags = NVCC_FLAGS + vflags + (["-Xptxas", "-v"] if verbose else []) + list(extra or [])
 
     def one(src):
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         unit = flags + (FAST_FP32_FLAGS if os.path.basename(src) in FAST_FP32_UNITS else [])
         cmd = [cc] + ARCH + unit + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,13 +83,13 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 3) batch_kernel(Batc
         __syncthreads();
         const long long it = next_item;   // every thread reads it before run_item's first barrier
         if (it >= ba.total_items) break;
-        const ItemRef ref = ba.order[it];
-        const BoxDesc& bd = ba.boxes[ref.box];
+        const ItemRef ref = ba.order[MHD_IDX(it, ba.total_items, ba.status)];
+        const BoxDesc& bd = ba.boxes[MHD_IDX(ref.box, ba.nbox, ba.status)];
         const StageArgs a = box_stage_args(ba, bd, stage, step);
         if (stage == 1) StageKernel<PREC, 1, TX, TY>::run_item(bd.g, a, ref.local, smem_raw);
         else StageKernel<PREC, 2, TX, TY>::run_item(bd.g, a, ref.local, smem_raw);

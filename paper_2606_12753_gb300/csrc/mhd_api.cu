@@ -1,6 +1,7 @@
 // C ABI of the MHD hot path: handle, device buffers, launches, reductions.
 #include <cuda.h>   // tensor-map types; the encoder itself is fetched from the driver at run time
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>   // header-only ranges; no cost unless a profiler is attached
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -392,6 +393,13 @@ static const TmaMaps* tma_for(const mhd_handle* h, const void* win) {
   return nullptr;
 }
 
+// NVTX range over one host entry point (seen by Nsight Systems as the call's
+// span on the host timeline; the kernels it enqueues appear beneath it)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 static long long face_count(const Geo& g, int d) {
   long long n[3] = {g.n[0], g.n[1], g.n[2]};
   n[d] = g.nf[d];
@@ -657,6 +665,7 @@ static int check_status(mhd_handle* h) {
   unsigned st = *(unsigned*)((unsigned long long*)h->pinned + 3);
   if (st & ST_NONFINITE) return fail(h, MHD_ERR_NONFINITE, "non-finite state value met on the device");
   if (st & ST_TIMEOUT) return fail(h, MHD_ERR_TIMEOUT, "a device wait timed out (barrier or plane copy)");
+  if (st & ST_BOUNDS) return fail(h, MHD_ERR_BOUNDS, "a kernel index left its array (bounds-checked build)");
   if (h->cfg.floor_policy == MHD_FLOOR_ERROR) {
     const unsigned long long* hp = (const unsigned long long*)h->pinned;
     unsigned long long hits = hp[8 + C_RHO_FLOOR] + hp[8 + C_P_FLOOR];
@@ -738,6 +747,7 @@ static cudaError_t copy_state_async(const mhd_handle* h, bool in, char* dev, voi
 
 extern "C" int mhd_stream_step(mhd_handle* h, const void* const cell_in[5], const void* const face_in[3],
                                void* cell_out[5], void* face_out[3], double dt) {
+  NvtxRange nvtx_range("mhd_stream_step");
   if (!h) return MHD_ERR_INVALID;
   if (!cell_in || !face_in || !cell_out || !face_out) return fail(h, MHD_ERR_INVALID, "null state pointer array");
   for (int v = 0; v < 5; ++v)
@@ -777,6 +787,7 @@ extern "C" int mhd_stream_sync(mhd_handle* h) {
 }
 
 extern "C" int mhd_step_async(mhd_handle* h, double dt, int nsteps) {
+  NvtxRange nvtx_range("mhd_step_async");
   if (!h) return MHD_ERR_INVALID;
   if (nsteps < 0) return fail(h, MHD_ERR_INVALID, "nsteps must be >= 0");
   if (dt != dt) return fail(h, MHD_ERR_INVALID, "dt is NaN");
@@ -786,6 +797,7 @@ extern "C" int mhd_step_async(mhd_handle* h, double dt, int nsteps) {
 }
 
 extern "C" int mhd_step(mhd_handle* h, double dt, int nsteps) {
+  NvtxRange nvtx_range("mhd_step");
   if (!h) return MHD_ERR_INVALID;
   if (nsteps < 0) return fail(h, MHD_ERR_INVALID, "nsteps must be >= 0");
   if (dt != dt) return fail(h, MHD_ERR_INVALID, "dt is NaN");
@@ -807,6 +819,7 @@ extern "C" int mhd_step(mhd_handle* h, double dt, int nsteps) {
 }
 
 extern "C" int mhd_rhs(mhd_handle* h, void* cell[5], void* face[3], int on_device) {
+  NvtxRange nvtx_range("mhd_rhs");
   if (!h) return MHD_ERR_INVALID;
   if (int rc = need_switch(h)) return rc;
   cudaError_t e = ensure_prims(h);
@@ -983,6 +996,9 @@ cudaError_t batch_set_smem_fp64(int, int, size_t);
 cudaError_t batch_set_smem_mixed(int, int, size_t);
 cudaError_t batch_set_smem_fp32(int, int, size_t);
 int batch_max_blocks_fp64(int, int, size_t);
+size_t batch_smem_bytes_fp64(int, int);
+size_t batch_smem_bytes_mixed(int, int);
+size_t batch_smem_bytes_fp32(int, int);
 int batch_max_blocks_mixed(int, int, size_t);
 int batch_max_blocks_fp32(int, int, size_t);
 
@@ -998,6 +1014,13 @@ cudaError_t batch_set_smem(int prec, int tx, int ty, size_t bytes) {
     case P_FP64: return batch_set_smem_fp64(tx, ty, bytes);
     case P_MIXED: return batch_set_smem_mixed(tx, ty, bytes);
     default: return batch_set_smem_fp32(tx, ty, bytes);
+  }
+}
+static size_t batch_smem_bytes(int prec, int tx, int ty) {
+  switch (prec) {
+    case P_FP64: return batch_smem_bytes_fp64(tx, ty);
+    case P_MIXED: return batch_smem_bytes_mixed(tx, ty);
+    default: return batch_smem_bytes_fp32(tx, ty);
   }
 }
 int batch_max_blocks_per_sm(int prec, int tx, int ty, size_t smem) {
@@ -1072,7 +1095,7 @@ static void drop_graph(mhd_batch* b) {
 static int batch_apply_tile(mhd_batch* b, int tx, int ty, int tz) {
   if (!stage_tile_supported(b->prec, tx, ty) || batch_max_blocks_per_sm(b->prec, tx, ty, 0) < 0)
     return bfail(b, MHD_ERR_INVALID, "tile %dx%d not available for the batch kernel", tx, ty);
-  const size_t smem = stage_smem_bytes(b->prec, tx, ty);
+  const size_t smem = batch_smem_bytes(b->prec, tx, ty);
   if (smem == 0 || smem > 227 * 1024) return bfail(b, MHD_ERR_INVALID, "tile %dx%d not available", tx, ty);
   cudaError_t e = batch_set_smem(b->prec, tx, ty, smem);
   if (e) return bfail(b, MHD_ERR_INVALID, "tile %dx%d is not instantiated for the batch kernel: %s", tx, ty,
@@ -1348,17 +1371,19 @@ static int batch_check(mhd_batch* b) {
   BCUDA_TRY(b, cudaMemcpyAsync(hp, b->words, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
   BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
   const unsigned st = *(unsigned*)(hp + 3);
-  if (st & (ST_TIMEOUT | ST_NONFINITE)) {
+  if (st & (ST_TIMEOUT | ST_NONFINITE | ST_BOUNDS)) {
     // report once, then clear so that the handle can be reused
     BCUDA_TRY(b, cudaMemsetAsync(b->status, 0, sizeof(unsigned), b->stream));
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
     if (st & ST_TIMEOUT) return bfail(b, MHD_ERR_TIMEOUT, "device-wide barrier of the persistent launch timed out");
+    if (st & ST_BOUNDS) return bfail(b, MHD_ERR_BOUNDS, "a kernel index left its array (bounds-checked build)");
     return bfail(b, MHD_ERR_NONFINITE, "non-finite state value met on the device");
   }
   return MHD_OK;
 }
 
 extern "C" int mhd_batch_step_async(mhd_batch* b, double dt, int nsteps) {
+  NvtxRange nvtx_range("mhd_batch_step_async");
   if (!b) return MHD_ERR_INVALID;
   if (nsteps < 1) return bfail(b, MHD_ERR_INVALID, "nsteps must be >= 1");
   if (dt != dt) return bfail(b, MHD_ERR_INVALID, "dt is NaN");
@@ -1366,6 +1391,7 @@ extern "C" int mhd_batch_step_async(mhd_batch* b, double dt, int nsteps) {
 }
 
 extern "C" int mhd_batch_step(mhd_batch* b, double dt, int nsteps) {
+  NvtxRange nvtx_range("mhd_batch_step");
   int rc = mhd_batch_step_async(b, dt, nsteps);
   if (rc) return rc;
   return batch_check(b);
@@ -1505,7 +1531,7 @@ extern "C" int mhd_batch_autotune(mhd_batch* b, int trial_steps, const char* cac
     }
   }
   static const int cand_xy[][2] = {{16, 8}, {16, 16}, {32, 8}, {24, 8}, {8, 8}};
-  static const int cand_z[] = {16, 32, 64};
+  static const int cand_z[] = {16, 32, 64, 128};
   int maxnz = 1;
   for (int i = 0; i < b->nbox; ++i) maxnz = b->cfg[i].nz > maxnz ? b->cfg[i].nz : maxnz;
   cudaEvent_t e0, e1;
@@ -1513,7 +1539,7 @@ extern "C" int mhd_batch_autotune(mhd_batch* b, int trial_steps, const char* cac
   cudaEventCreate(&e1);
   best_ms = -1.0;
   for (const auto& xy : cand_xy) {
-    for (int zi = 0; zi < 3; ++zi) {
+    for (int zi = 0; zi < 4; ++zi) {
       const int tz = cand_z[zi];
       if (zi > 0 && cand_z[zi - 1] >= maxnz) break;
       if (batch_apply_tile(b, xy[0], xy[1], tz) != MHD_OK) break;   // tile not instantiated

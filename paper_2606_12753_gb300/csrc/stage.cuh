@@ -36,8 +36,43 @@ template <> struct Prec<P_FP32> { using S = float; using R = float; using K = fl
 template <bool C, class A, class B> struct Pick { using type = A; };
 template <class A, class B> struct Pick<false, A, B> { using type = B; };
 
-// status bits
-enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+// status bits (ST_BOUNDS: bounds-checked builds only)
+enum { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 4 };
+
+// Index checks of the bounds-checked build (MHD_BOUNDS_CHECK): an index
+// outside [0, n) raises ST_BOUNDS in the status word and is replaced by 0,
+// so the access stays inside its array and the kernel runs to its end (no
+// trap).  In the normal build the index passes through unchanged.
+__device__ __forceinline__ long long bounds_checked(long long i, long long n, unsigned* status) {
+  if (i < 0 || i >= n) {
+    atomicOr(status, (unsigned)ST_BOUNDS);
+    return 0;
+  }
+  return i;
+}
+#ifdef MHD_BOUNDS_CHECK
+// shared-memory index checks record into one flag per CTA, folded into the
+// status word at the end of each work item
+__device__ __forceinline__ unsigned* cta_bounds_flag() {
+  __shared__ unsigned flag;
+  return &flag;
+}
+__device__ __forceinline__ int smem_checked(int i, int n) {
+  if (i < 0 || i >= n) {
+    *cta_bounds_flag() = 1u;
+    return 0;
+  }
+  return i;
+}
+#define MHD_SIDX(i, n) ::mhd::smem_checked((i), (n))
+#define MHD_IDX(i, n, status) ::mhd::bounds_checked((i), (n), (status))
+#define MHD_ASSERT_RANGE(i, lo, hi, status) \
+  do { if ((i) < (lo) || (i) >= (hi)) atomicOr((status), (unsigned)::mhd::ST_BOUNDS); } while (0)
+#else
+#define MHD_SIDX(i, n) (i)
+#define MHD_IDX(i, n, status) (i)
+#define MHD_ASSERT_RANGE(i, lo, hi, status) do { } while (0)
+#endif
 // counters
 enum { C_RHO_FLOOR = 0, C_P_FLOOR = 1, C_HLL = 2, C_HLLD = 3, C_TMA = 4, C_NCOUNT = 8 };
 // number of primitive arrays

@@ -134,11 +134,13 @@ __device__ __forceinline__ double face_value(const Geo& g, const StageArgs& a, d
   int len[3] = {g.n[0], g.n[1], g.n[2]};
   len[d] = g.nf[d];
   c[d] = fr.a;
-  const long long ia = g.face_off[d] + c[0] + (long long)len[0] * (c[1] + (long long)len[1] * c[2]);
+  const long long ia = MHD_IDX(g.face_off[d] + c[0] + (long long)len[0] * (c[1] + (long long)len[1] * c[2]),
+                               g.total, a.status);
   const double f0 = cons_at<PREC, STAGE>(a, ia, dt);
   if (!fr.t) return f0;
   c[d] = fr.b;
-  const long long ib = g.face_off[d] + c[0] + (long long)len[0] * (c[1] + (long long)len[1] * c[2]);
+  const long long ib = MHD_IDX(g.face_off[d] + c[0] + (long long)len[0] * (c[1] + (long long)len[1] * c[2]),
+                               g.total, a.status);
   const double f1 = cons_at<PREC, STAGE>(a, ib, dt);
   return f0 + (double)fr.t * (f1 - f0);
 }
@@ -164,11 +166,19 @@ constexpr bool slopes_in_smem() {
   return MODE == FM_CHAR || (PREC == P_FP64 && MODE == FM_PLAIN && TX * TY <= 128);
 }
 
-// Ring x-offset of a kernel: the plain kernels with 4-byte primitives (mixed,
-// FP32) pad the ring rows so that interior planes can arrive by TMA.
-template <int PREC, int MODE>
+// Whether a kernel takes interior planes by TMA: the plain single-box stage
+// kernels with 4-byte primitives (mixed, FP32).  The batch kernel, whose
+// small outflow boxes have few interior tiles, gathers every plane.
+template <int PREC, int MODE, bool SINGLE_BOX>
+__host__ __device__ constexpr bool tma_planes() {
+  return SINGLE_BOX && PREC != P_FP64 && MODE == FM_PLAIN;
+}
+
+// Ring x-offset of a kernel: kernels with TMA planes pad the ring rows (see
+// Tile); all others keep the 2-cell halo.
+template <int PREC, int MODE, bool SINGLE_BOX>
 __host__ __device__ constexpr int ring_xo() {
-  return PREC != P_FP64 && MODE == FM_PLAIN ? 4 : 2;
+  return tma_planes<PREC, MODE, SINGLE_BOX>() ? 4 : 2;
 }
 
 // SPLIT: the update phase splits each cell between two threads (face group
@@ -177,7 +187,8 @@ __host__ __device__ constexpr int ring_xo() {
 // forms, slower for FP32 (its update phase carries no FP64 work) and for the
 // batch kernel.  PREFETCH (split form only): phase D's stored values are
 // loaded into registers before phase C.
-template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false>
+template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false,
+          bool SINGLE_BOX = false>
 struct StageKernel {
   static constexpr bool LEARN = MODE == FM_LEARNED;
   static constexpr bool CHAR = MODE == FM_CHAR;
@@ -185,11 +196,11 @@ struct StageKernel {
   using R = typename Prec<PREC>::R;
   using S = typename Prec<PREC>::S;
   using K = typename Prec<PREC>::K;
-  using T = Tile<TX, TY, ring_xo<PREC, MODE>()>;
+  using T = Tile<TX, TY, ring_xo<PREC, MODE, SINGLE_BOX>()>;
   static constexpr int W = T::W;
   static constexpr int XO = T::XOFF;
   // TMA planes: plain kernels with 4-byte primitives
-  static constexpr bool kTMA = MODE == FM_PLAIN && PREC != P_FP64;
+  static constexpr bool kTMA = tma_planes<PREC, MODE, SINGLE_BOX>();
   static_assert(!kTMA || ((8 * T::nR * sizeof(R)) % 128 == 0 && (T::oBN * sizeof(R)) % 128 == 0 &&
                           (T::nBslot * sizeof(R)) % 128 == 0 && (T::W * sizeof(R)) % 16 == 0),
                 "TMA ring slots must start on 128-byte boundaries and rows span whole 16-byte units");
@@ -218,7 +229,8 @@ struct StageKernel {
       R w[NW];
       const long long s = (long long)colc[x] + (long long)g.n[0] * ((long long)rowc[y] + (long long)g.n[1] * ck);
 #pragma unroll
-      for (int v = 0; v < NW; ++v) w[v] = Win[v * g.ncell + s];
+      for (int v = 0; v < NW; ++v) w[v] = Win[MHD_IDX(v * g.ncell + s, NW * g.ncell, a.status)];
+      MHD_ASSERT_RANGE(r, 0, T::nR, a.status);
       if (!inside) {
         // outflow ghost: rho, v, p of the nearest interior cell; along each
         // axis on which the cell is a ghost, the normal field on its faces is
@@ -239,7 +251,7 @@ struct StageKernel {
       for (int v = 0; v < 8; ++v) P[v * T::nR + r] = w[v];
       if (write_bn && y >= 1 && y <= TY + 2) {   // the lower-face rows -1..TY
 #pragma unroll
-        for (int d = 0; d < 3; ++d) BN[d * T::nB + bn_of(r)] = w[8 + d];
+        for (int d = 0; d < 3; ++d) BN[d * T::nB + MHD_IDX(bn_of(r), T::nB, a.status)] = w[8 + d];
       }
     }
   }
@@ -264,7 +276,17 @@ struct StageKernel {
     }
   }
   static __device__ __forceinline__ void tma_issue(const TmaMaps& tm, R* sm, unsigned long long* mbar, int m, int ck,
-                                                   int gi0, int gj0, bool with_bn) {
+                                                   int gi0, int gj0, bool with_bn, const Geo& g, unsigned* status) {
+    // the columns and rows the ring uses lie inside the box's array (the
+    // padding columns may not: the copy fills them with zeros)
+    MHD_ASSERT_RANGE(gi0 - 2, 0, g.n[0], status);
+    MHD_ASSERT_RANGE(gi0 + TX + 1, 0, g.n[0], status);
+    MHD_ASSERT_RANGE(gj0 - 2, 0, g.n[1], status);
+    MHD_ASSERT_RANGE(gj0 + TY + 1, 0, g.n[1], status);
+    MHD_ASSERT_RANGE(ck, 0, g.n[2], status);
+    MHD_ASSERT_RANGE((gi0 - XO) & 3, 0, 1, status);   // 16-byte first column
+    (void)g;
+    (void)status;
     const unsigned bar = smem_u32(mbar + (m & 3));
     const unsigned bytes = (unsigned)((8 * T::nR + (with_bn ? 3 * T::nB : 0)) * sizeof(R));
     unsigned long long state;
@@ -353,7 +375,7 @@ struct StageKernel {
     for (int it = first + threadIdx.x; it < 3 * n; it += blockDim.x) {
       const int D = it / n, cidx = it - D * n;
       const int i = cidx % (TX + 2) - 1, j = cidx / (TX + 2) - 1;
-      const int r = (i + XO) + W * (j + 2);
+      const int r = MHD_SIDX(MHD_SIDX((i + XO) + W * (j + 2) - W - 1, T::nR - 2 * W - 2) + W + 1, T::nR);
       R c[3][7], out[7];
       R bnc = R(0);
       if (D == 0) {
@@ -398,10 +420,10 @@ struct StageKernel {
       const R* sb;
       if (w < nZ) {
         const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
-        const int r = (i + XO) + W * (j + 2);
+        const int r = MHD_SIDX((i + XO) + W * (j + 2), T::nR);
         gather<2>(sm + T::oP + (k & 3) * 8 * T::nR, T::nR, r, c1);
         gather<2>(sm + T::oP + ((k + 1) & 3) * 8 * T::nR, T::nR, r, c2);
-        bn = bn_slot(sm, k + 1)[2 * T::nB + bn_of(r)];
+        bn = bn_slot(sm, k + 1)[2 * T::nB + MHD_SIDX(bn_of(r), T::nB)];
         ia = ib = w;
         sa = sl + (2 + (k & 1)) * T::nSl;
         sb = sl + (2 + ((k + 1) & 1)) * T::nSl;
@@ -410,10 +432,10 @@ struct StageKernel {
       } else if (w < nZ + T::nX) {
         o = w - nZ;
         const int i = o % (TX + 1), j = o / (TX + 1) - 1;
-        const int r = (i + XO) + W * (j + 2);
+        const int r = MHD_SIDX(MHD_SIDX((i + XO) + W * (j + 2) - 1, T::nR - 1) + 1, T::nR);
         gather<0>(Pq, T::nR, r - 1, c1);
         gather<0>(Pq, T::nR, r, c2);
-        bn = BNq[bn_of(r)];
+        bn = BNq[MHD_SIDX(bn_of(r), T::nB)];
         ia = i + (TX + 2) * (j + 1);
         ib = ia + 1;
         sa = sb = sl;
@@ -421,10 +443,10 @@ struct StageKernel {
       } else {
         o = w - nZ - T::nX;
         const int i = o % (TX + 2) - 1, j = o / (TX + 2);
-        const int r = (i + XO) + W * (j + 2);
+        const int r = MHD_SIDX(MHD_SIDX((i + XO) + W * (j + 2) - W, T::nR - W) + W, T::nR);
         gather<1>(Pq, T::nR, r - W, c1);
         gather<1>(Pq, T::nR, r, c2);
-        bn = BNq[T::nB + bn_of(r)];
+        bn = BNq[T::nB + MHD_SIDX(bn_of(r), T::nB)];
         ib = (i + 1) + (TX + 2) * (j + 1);
         ia = ib - (TX + 2);
         sa = sb = sl + T::nSl;
@@ -476,10 +498,10 @@ struct StageKernel {
     const R* BNq = bn_slot(sm, q);
     if (w < nZ) {
       const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
-      const int r = (i + XO) + W * (j + 2);
+      const int r = MHD_SIDX((i + XO) + W * (j + 2), T::nR);
 #pragma unroll
       for (int s = 0; s < 4; ++s) gather<2>(sm + T::oP + ((k - 1 + s) & 3) * 8 * T::nR, T::nR, r, c[s]);
-      bn = bn_slot(sm, k + 1)[2 * T::nB + bn_of(r)];
+      bn = bn_slot(sm, k + 1)[2 * T::nB + MHD_SIDX(bn_of(r), T::nB)];
       if (bnc) {
         bnc[0] = sm[T::oP + (k & 3) * 8 * T::nR + 7 * T::nR + r];
         bnc[1] = sm[T::oP + ((k + 1) & 3) * 8 * T::nR + 7 * T::nR + r];
@@ -490,10 +512,10 @@ struct StageKernel {
     if (w < nZ + T::nX) {
       o = w - nZ;
       const int i = o % (TX + 1), j = o / (TX + 1) - 1;
-      const int r = (i + XO) + W * (j + 2);
+      const int r = MHD_SIDX(MHD_SIDX((i + XO) + W * (j + 2) - 2, T::nR - 3) + 2, T::nR);
 #pragma unroll
       for (int s = 0; s < 4; ++s) gather<0>(Pq, T::nR, r - 2 + s, c[s]);
-      bn = BNq[bn_of(r)];
+      bn = BNq[MHD_SIDX(bn_of(r), T::nB)];
       if (bnc) {
         bnc[0] = Pq[5 * T::nR + r - 1];
         bnc[1] = Pq[5 * T::nR + r];
@@ -502,10 +524,10 @@ struct StageKernel {
     }
     o = w - nZ - T::nX;
     const int i = o % (TX + 2) - 1, j = o / (TX + 2);
-    const int r = (i + XO) + W * (j + 2);
+    const int r = MHD_SIDX(MHD_SIDX((i + XO) + W * (j + 2) - 2 * W, T::nR - 3 * W) + 2 * W, T::nR);
 #pragma unroll
     for (int s = 0; s < 4; ++s) gather<1>(Pq, T::nR, r + (s - 2) * W, c[s]);
-    bn = BNq[T::nB + bn_of(r)];
+    bn = BNq[T::nB + MHD_SIDX(bn_of(r), T::nB)];
     if (bnc) {
       bnc[0] = Pq[6 * T::nR + r - W];
       bnc[1] = Pq[6 * T::nR + r];
@@ -524,6 +546,7 @@ struct StageKernel {
     if (D == 2) { H = sm + T::oHZ; C = sm + T::oZC; n = T::nZ; }
     else if (D == 0) { H = sm + T::oHX; C = sm + T::oXC + (q & 1) * 3 * T::nX; n = T::nX; }
     else { H = sm + T::oHY; C = sm + T::oYC + (q & 1) * 3 * T::nY; n = T::nY; }
+    o = MHD_SIDX(o, n);
     H[0 * n + o] = f[0];
     H[(1 + D) * n + o] = f[1];
     H[(1 + (D + 1) % 3) * n + o] = f[2];
@@ -884,9 +907,12 @@ struct StageKernel {
     const bool carried = zc && zc->have;
     const R lz0 = carried ? zc->l : -((EY0[e + 1] - EY0[e]) * idx - (EX0[e + (TX + 1)] - EX0[e]) * idy);
     const R lz1 = -((EY1[e + 1] - EY1[e]) * idx - (EX1[e + (TX + 1)] - EX1[e]) * idy);
-    const long long fx0 = face_index(g, gi, gj, k, 0), fx1 = face_index(g, gi, gj, k, 1);
-    const long long fy0 = face_index(g, gi, gj, k, 2), fy1 = face_index(g, gi, gj, k, 3);
-    const long long fz0 = face_index(g, gi, gj, k, 4), fz1 = face_index(g, gi, gj, k, 5);
+    const long long fx0 = MHD_IDX(face_index(g, gi, gj, k, 0), g.total, a.status);
+    const long long fx1 = MHD_IDX(face_index(g, gi, gj, k, 1), g.total, a.status);
+    const long long fy0 = MHD_IDX(face_index(g, gi, gj, k, 2), g.total, a.status);
+    const long long fy1 = MHD_IDX(face_index(g, gi, gj, k, 3), g.total, a.status);
+    const long long fz0 = MHD_IDX(face_index(g, gi, gj, k, 4), g.total, a.status);
+    const long long fz1 = MHD_IDX(face_index(g, gi, gj, k, 5), g.total, a.status);
     const S bx0 = pre ? advance(pre[0], lx0, dt) : advance(a, fx0, lx0, dt);
     const S bx1 = pre ? advance(pre[1], lx1, dt) : advance(a, fx1, lx1, dt);
     const S by0 = pre ? advance(pre[2], ly0, dt) : advance(a, fy0, ly0, dt);
@@ -915,8 +941,9 @@ struct StageKernel {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const R l = DU[v * T::nC + c];
-      const S nv = pre ? advance(pre[v], l, dt) : advance(a, v * g.ncell + s, l, dt);
-      emit(a, v * g.ncell + s, l, nv);
+      const long long gidx = MHD_IDX(v * g.ncell + s, 5 * g.ncell, a.status);
+      const S nv = pre ? advance(pre[v], l, dt) : advance(a, gidx, l, dt);
+      emit(a, gidx, l, nv);
       u[v] = (double)nv;
     }
   }
@@ -933,7 +960,7 @@ struct StageKernel {
     np += hp;
     if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
 #pragma unroll
-    for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
+    for (int v = 0; v < NW; ++v) Wout[MHD_IDX(v * g.ncell + s, NW * g.ncell, a.status)] = w[v];
     if (StageTraits<STAGE>::last) {
       const R sp = cfl_speed<R>(g, w);
       smax = sp > smax ? sp : smax;
@@ -962,11 +989,11 @@ struct StageKernel {
     if (t >= T::nC) {
       const long long s = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) p.o[v] = fetch(a, v * g.ncell + s);
+      for (int v = 0; v < 5; ++v) p.o[v] = fetch(a, MHD_IDX(v * g.ncell + s, 5 * g.ncell, a.status));
     } else {
 #pragma unroll
       for (int m = 0; m < 6; ++m)
-        if (m != 4 || !carried) p.o[m] = fetch(a, face_index(g, gi, gj, k, m));
+        if (m != 4 || !carried) p.o[m] = fetch(a, MHD_IDX(face_index(g, gi, gj, k, m), g.total, a.status));
     }
   }
 
@@ -1077,6 +1104,9 @@ struct StageKernel {
 
     if (StageTraits<STAGE>::first && item == 0 && threadIdx.x == 0) *a.nextword = 0ull;
     __syncthreads();   // the previous item of this CTA may still read the tables
+#ifdef MHD_BOUNDS_CHECK
+    if (threadIdx.x == 0) *cta_bounds_flag() = 0u;
+#endif
     for (int t = threadIdx.x; t < T::W + T::H; t += blockDim.x) {
       if (t < T::W) colc[t] = wrapc(gi0 - XO + t, g.n[0], g.bc[0]);
       else rowc[t - T::W] = wrapc(gj0 - 2 + (t - T::W), g.n[1], g.bc[1]);
@@ -1125,6 +1155,7 @@ struct StageKernel {
       ZCarry zc{S(0), R(0), false};
       update_plane(g, a, sm, sdt, gi0, gj0, 0, nrho, np, bad, smax, zc);
       finish(a, nrho, np, nh, nd, bad, smax);
+      fold_bounds_flag(a);
       return;
     }
     // TMA planes: every in-range plane of an interior tile (no periodic wrap,
@@ -1142,7 +1173,7 @@ struct StageKernel {
     for (int m = kb - 2; m <= kb; ++m) {
       if (plane_tma(m)) {
         if (threadIdx.x == 0) {
-          tma_issue(*tm, sm, mbar, m, wrapc(m, g.n[2], g.bc[2]), gi0, gj0, m != kb - 2);
+          tma_issue(*tm, sm, mbar, m, wrapc(m, g.n[2], g.bc[2]), gi0, gj0, m != kb - 2, g, a.status);
           ++ntma;
         }
       } else {
@@ -1165,7 +1196,7 @@ struct StageKernel {
     // a TMA plane is issued as soon as the flux phase has freed its slot:
     // plane k + 3 goes where plane k - 1 was, and lands during phases C, D
     if (plane_tma(kb + 1) && threadIdx.x == 0) {
-      tma_issue(*tm, sm, mbar, kb + 1, wrapc(kb + 1, g.n[2], g.bc[2]), gi0, gj0, true);
+      tma_issue(*tm, sm, mbar, kb + 1, wrapc(kb + 1, g.n[2], g.bc[2]), gi0, gj0, true, g, a.status);
       ++ntma;
     }
     ZCarry zc{S(0), R(0), false};   // face group: upper z-face of the previous plane
@@ -1187,7 +1218,7 @@ struct StageKernel {
       }
       __syncthreads();
       if (k + 3 <= ke + 1 && plane_tma(k + 3) && threadIdx.x == 0) {
-        tma_issue(*tm, sm, mbar, k + 3, wrapc(k + 3, g.n[2], g.bc[2]), gi0, gj0, true);
+        tma_issue(*tm, sm, mbar, k + 3, wrapc(k + 3, g.n[2], g.bc[2]), gi0, gj0, true, g, a.status);
         ++ntma;
       }
       Pre pre;
@@ -1201,6 +1232,17 @@ struct StageKernel {
 
     finish(a, nrho, np, nh, nd, bad, smax);
     if (ntma && threadIdx.x == 0) atomicAdd(&a.counters[C_TMA], (unsigned long long)ntma);
+    fold_bounds_flag(a);
+  }
+
+  // bounds-checked build: the CTA's shared-memory index flag into the status word
+  static __device__ __forceinline__ void fold_bounds_flag(const StageArgs& a) {
+#ifdef MHD_BOUNDS_CHECK
+    __syncthreads();
+    if (threadIdx.x == 0 && *cta_bounds_flag()) atomicOr(a.status, (unsigned)ST_BOUNDS);
+#else
+    (void)a;
+#endif
   }
 };
 
@@ -1226,8 +1268,8 @@ template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_blocks<PREC, TX, TY>())
     stage_kernel(Geo g, StageArgs a, const __grid_constant__ TmaMaps tm) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>(), PREC == P_FP64>::run_item(g, a, blockIdx.x,
-                                                                                                    smem_raw, &tm);
+  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>(), PREC == P_FP64, true>::run_item(
+      g, a, blockIdx.x, smem_raw, &tm);
 }
 
 // The same stage with the learned HLL/HLLD face switch.
@@ -1275,6 +1317,13 @@ __global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
     const int ih = i + 1 < g.nf[0] ? i + 1 : 0;
     R w[NW];
     int hr, hp;
+#ifdef MHD_BOUNDS_CHECK
+    {
+      const long long idx[10] = {4 * g.ncell + s, xbase + i, xbase + ih, ybase_lo + i, ybase_hi + i,
+                                 zbase_lo + i, zbase_hi + i, s, g.face_off[1] - 1, g.total - 1};
+      for (int q = 0; q < 7; ++q) (void)bounds_checked(idx[q], g.total, a.status);
+    }
+#endif
     recover<PREC>(g, (double)U[s], (double)U[g.ncell + s], (double)U[2 * g.ncell + s], (double)U[3 * g.ncell + s],
                   (double)U[4 * g.ncell + s], (double)U[xbase + i], (double)U[xbase + ih], (double)U[ybase_lo + i],
                   (double)U[ybase_hi + i], (double)U[zbase_lo + i], (double)U[zbase_hi + i], w, hr, hp);
@@ -1282,7 +1331,7 @@ __global__ void __launch_bounds__(128) prims_kernel(Geo g, StageArgs a) {
     np += hp;
     if (!(isfinite(w[4]) && isfinite(w[1] + w[2] + w[3]) && isfinite(w[5] + w[6] + w[7]))) bad = true;
 #pragma unroll
-    for (int v = 0; v < NW; ++v) Wout[v * g.ncell + s] = w[v];
+    for (int v = 0; v < NW; ++v) Wout[MHD_IDX(v * g.ncell + s, NW * g.ncell, a.status)] = w[v];
     const R sp = cfl_speed<R>(g, w);
     smax = sp > smax ? sp : smax;
   }

@@ -42,7 +42,7 @@ size_t MHD_UNIT_FN(smem_bytes)(int tx, int ty) {
   using S = Prec<MHD_UNIT_PREC>::S;
 #define X(TXv, TYv)                                                                                      \
   if (tx == TXv && ty == TYv)                                                                            \
-    return Tile<TXv, TYv, ring_xo<MHD_UNIT_PREC, FM_PLAIN>()>::bytes<                                    \
+    return Tile<TXv, TYv, ring_xo<MHD_UNIT_PREC, FM_PLAIN, true>()>::bytes<                              \
         R, S, slopes_in_smem<MHD_UNIT_PREC, FM_PLAIN, TXv, TYv>()>();
   MHD_TILES(X)
 #undef X
@@ -51,13 +51,13 @@ size_t MHD_UNIT_FN(smem_bytes)(int tx, int ty) {
 
 // characteristic reconstruction (16 x 8 tile) keeps its slopes in shared memory
 size_t MHD_UNIT_FN(smem_bytes_char)() {
-  return Tile<16, 8, ring_xo<MHD_UNIT_PREC, FM_CHAR>()>::bytes<Prec<MHD_UNIT_PREC>::R, Prec<MHD_UNIT_PREC>::S,
+  return Tile<16, 8, ring_xo<MHD_UNIT_PREC, FM_CHAR, true>()>::bytes<Prec<MHD_UNIT_PREC>::R, Prec<MHD_UNIT_PREC>::S,
                                                                true>();
 }
 
 // the learned switch (16 x 8 tile) queues its face items in shared memory
 size_t MHD_UNIT_FN(smem_bytes_learned)() {
-  return Tile<16, 8, ring_xo<MHD_UNIT_PREC, FM_LEARNED>()>::bytes<Prec<MHD_UNIT_PREC>::R,
+  return Tile<16, 8, ring_xo<MHD_UNIT_PREC, FM_LEARNED, true>()>::bytes<Prec<MHD_UNIT_PREC>::R,
                                                                   Prec<MHD_UNIT_PREC>::S, false, true>();
 }
 

@@ -18,6 +18,7 @@ from . import _build
 
 MHD_OK = 0
 MHD_ERR_INVALID, MHD_ERR_CUDA, MHD_ERR_NONFINITE, MHD_ERR_TIMEOUT, MHD_ERR_NOMEM, MHD_ERR_FLOOR = -1, -2, -3, -4, -5, -6
+MHD_ERR_BOUNDS = -7
 MHD_FLOOR_COUNT, MHD_FLOOR_ERROR = 0, 1
 MHD_COPY_AUTO, MHD_COPY_GATHER = 0, 1
 MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
@@ -77,8 +78,17 @@ EXPORTS = ["mhd_default_config", "mhd_create", "mhd_set_state", "mhd_get_state",
 _lib = None
 
 
+def library_variant() -> str:
+    """Which build of the library this process loads: "release", or
+    "bounds" (every kernel index checked) when MHD_LIBRARY_VARIANT says so."""
+    v = os.environ.get("MHD_LIBRARY_VARIANT", "release")
+    if v not in _build.VARIANTS:
+        raise RuntimeError(f"unknown MHD_LIBRARY_VARIANT {v!r} (one of {sorted(_build.VARIANTS)})")
+    return v
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.variant_path(library_variant())
 
 
 def load(build: bool = True):
@@ -86,11 +96,13 @@ def load(build: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    if build and _build.needs_build():
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
-    L = C.CDLL(_build.LIB)
+    variant = library_variant()
+    path = _build.variant_path(variant)
+    if build and _build.needs_build(variant):
+        _build.build(variant=variant)
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
     L.mhd_default_config.restype = None
     L.mhd_default_config.argtypes = [C.POINTER(mhd_config), C.c_int, C.c_int, C.c_int]
     L.mhd_create.restype = C.c_int
