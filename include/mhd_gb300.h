@@ -270,12 +270,15 @@ int mhd_get_stats(mhd_handle* h, mhd_stats* out);
  * two solvers (the flux arithmetic itself is never replaced).  The paper names
  * both solvers (Sec. 2.2, HLLD_Solver and HLL_Solver in Tables 2-4); the
  * network is this library's addition.  Inference and training use BF16
- * tensor-core MMAs with FP32 accumulation.
+ * tensor-core MMAs with FP32 accumulation: mlp_forward and mlp_backward run
+ * the 128-row products on the tcgen05 tensor cores (accumulators in tensor
+ * memory), the weight gradients (32 output rows) on warp-level MMAs.
  *
  * Parameter block: mlp_param_bytes() bytes of device memory, caller-owned:
  * FP32 master parameters in the order W1[32][16], b1[32], W2[32][32], b2[32],
  * W3[32], b3 (1633 values), followed by the bf16 copies of W1, W2, W3.
- * Features: 16 floats per face (see mhd_dump_faces); logits: 1 float.
+ * Features: 16 floats per face (see mhd_dump_faces), 16-byte aligned
+ * (MHD_ERR_INVALID otherwise); logits: 1 float.
  * All array arguments are device pointers; calls enqueue on cuda_stream.
  * ------------------------------------------------------------------------ */
 size_t mlp_param_bytes(void);

@@ -1,10 +1,11 @@
 // Learned HLL/HLLD face switch: a 16 -> 32 -> 32 -> 1 network (ReLU hidden
-// layers, sigmoid output) evaluated and trained with BF16 tensor-core MMAs
-// (mma.sync m16n8k16, FP32 accumulation).  One warp handles 32 faces: two
+// layers, sigmoid output).  Inside the stage kernels it runs per warp with
+// BF16 mma.sync m16n8k16 (FP32 accumulation) on the warp's 32 faces: two
 // 16-row tiles of the feature matrix times the transposed weight matrices.
 // The accumulator fragment of one layer is, after bias, ReLU and rounding to
 // bf16, exactly the A fragment of the next layer, so the hidden activations
-// never leave registers.
+// never leave registers.  Training-size forward and backward passes over
+// feature arrays run on the tcgen05 tensor cores (mlp.cu).
 //
 // Parameter block in device memory (all offsets in bytes, 16-aligned):
 //   float master[NPARAM]  W1[32][16], b1[32], W2[32][32], b2[32], W3[32], b3
@@ -76,8 +77,7 @@ __host__ __device__ __forceinline__ void face_features(const R* wl, const R* wr,
 // every lane the logit of face `lane`.  wb: bf16 weights, master: the FP32
 // block (b1, b2, b3 read from it).  All 32 lanes must call it.
 __device__ __forceinline__ float mlp_forward_frags(const uint32_t (&a1)[2][4], const uint16_t* wb,
-                                                   const float* master, float* h1_out = nullptr,
-                                                   float* h2_out = nullptr) {
+                                                   const float* master) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const uint32_t* W = reinterpret_cast<const uint32_t*>(wb);
@@ -103,12 +103,6 @@ __device__ __forceinline__ float mlp_forward_frags(const uint32_t (&a1)[2][4], c
       a2[ks][2] = pack_bf16x2(fmaxf(h1[2 * ks + 1][0], 0.f), fmaxf(h1[2 * ks + 1][1], 0.f));
       a2[ks][3] = pack_bf16x2(fmaxf(h1[2 * ks + 1][2], 0.f), fmaxf(h1[2 * ks + 1][3], 0.f));
     }
-    if (h1_out) {
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h1_out[(mt * 4 + nt) * 4 + q] = h1[nt][q];
-    }
     float h2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
@@ -119,12 +113,6 @@ __device__ __forceinline__ float mlp_forward_frags(const uint32_t (&a1)[2][4], c
       for (int ks = 0; ks < 2; ++ks)
         mma_16816(h2[nt], a2[ks], W[(MLP_WB_W2 + n * 32 + ks * 16 + 2 * t) >> 1],
                   W[(MLP_WB_W2 + n * 32 + ks * 16 + 2 * t + 8) >> 1]);
-    }
-    if (h2_out) {
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h2_out[(mt * 4 + nt) * 4 + q] = h2[nt][q];
     }
     // layer 3: [16 x 32] x W3^T [32 x 1] (padded to 8 columns)
     float z[4];
@@ -154,25 +142,6 @@ __device__ __forceinline__ float mlp_forward_frags(const uint32_t (&a1)[2][4], c
   const float v11 = __shfl_sync(0xffffffffu, z1hi, src);
   const float lo = mt == 0 ? v00 : v10, hi = mt == 0 ? v01 : v11;
   return r < 8 ? lo : hi;
-}
-
-// Forward pass for 32 faces whose features (bf16, row-major [32][16]) are in
-// shared memory F.
-__device__ __forceinline__ float mlp_forward_warp(const uint16_t* F, const uint16_t* wb, const float* master,
-                                                  float* h1_out = nullptr, float* h2_out = nullptr) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const uint32_t* F32 = reinterpret_cast<const uint32_t*>(F);
-  uint32_t a[2][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int r0 = mt * 16 + g, r1 = r0 + 8;
-    a[mt][0] = F32[(r0 * 16 + 2 * t) >> 1];
-    a[mt][1] = F32[(r1 * 16 + 2 * t) >> 1];
-    a[mt][2] = F32[(r0 * 16 + 2 * t + 8) >> 1];
-    a[mt][3] = F32[(r1 * 16 + 2 * t + 8) >> 1];
-  }
-  return mlp_forward_frags(a, wb, master, h1_out, h2_out);
 }
 
 // Forward pass for 32 faces whose features each lane holds in registers

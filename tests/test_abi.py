@@ -224,3 +224,13 @@ def test_error_text_without_a_handle_is_per_thread():
     t.join()
     assert "gamma" in mine and seen["before"] == "" and "cfl" in seen["after"]
     assert mhd.mhd_last_error(None) == mine
+
+
+def test_mlp_feature_rows_must_be_16_byte_aligned():
+    """The tensor-core kernels read each feature row with 16-byte loads, so a
+    misaligned feature pointer is refused on the host before any launch."""
+    for call in (lambda: mhd.mlp_forward(256, 260, 10, 512),
+                 lambda: mhd.mlp_backward(256, 264, 512, 10, 768)):
+        with pytest.raises(mhd.MHDError) as ei:
+            call()
+        assert ei.value.code == mhd.MHD_ERR_INVALID
