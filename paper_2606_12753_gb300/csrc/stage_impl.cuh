@@ -661,7 +661,14 @@ struct StageKernel {
     const R* HX = sm + T::oHX;
     const R* HY = sm + T::oHY;
     const R* HZ = sm + T::oHZ;
-    for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
+    // The edge slots go to whole warps from warp 0 on and the cells to the
+    // warps after them, when at least two warps are left for the cells:
+    // otherwise the first warps would form both and the last ones idle.
+    constexpr int kEdgeThreads = (T::nE + 31) / 32 * 32;
+    const bool apart = (int)blockDim.x >= kEdgeThreads + 64;
+    const int c0 = apart ? (int)threadIdx.x - kEdgeThreads : (int)threadIdx.x;
+    const int cstep = apart ? (int)blockDim.x - kEdgeThreads : (int)blockDim.x;
+    for (int c = c0 < 0 ? T::nC : c0; c < T::nC; c += cstep) {
       const int i = c % TX, j = c / TX;
       const int iz = (i + 1) + (TX + 2) * (j + 1);
       const int ixm = i + (TX + 1) * (j + 1), ixp = ixm + 1;
@@ -686,7 +693,7 @@ struct StageKernel {
     R* EX1 = sm + T::oEXY + sk1 * 2 * T::nE;   // edges at k+1/2
     R* EY1 = EX1 + T::nE;
     constexpr int nX = T::nX, nY = T::nY, nZ = T::nZ;
-    for (int e = threadIdx.x; e < T::nE; e += blockDim.x) {
+    for (int e = threadIdx.x; e < T::nE; e += apart ? kEdgeThreads : (int)blockDim.x) {
       const int i = e % (TX + 1), j = e / (TX + 1);
       {  // E_z at (i-1/2, j-1/2), plane k
         const int xa = i + (TX + 1) * j, xb = xa + (TX + 1);
