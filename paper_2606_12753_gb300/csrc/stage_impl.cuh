@@ -66,7 +66,7 @@ struct Tile {
   static constexpr int nItems = nZ + nX + nY;
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
-  static constexpr int nI = W + H + 6;   // column/row maps, switch counters, the stage's dt
+  static constexpr int nI = W + H + 8;   // column/row maps, switch counters, the stage's dt, flux tickets
   // then four mbarriers (8 bytes each), one per ring slot, for TMA planes
   // per-cell half slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
   // x and y slopes of the current plane, z slopes of two planes (by parity)
@@ -183,10 +183,12 @@ __host__ __device__ constexpr int ring_xo() {
 
 // SPLIT: the update phase splits each cell between two threads (face group
 // and conserved group, named-barrier hand-over); the CTA then needs at least
-// two threads per cell of a plane.  Measured faster for the mixed and FP64
-// forms, slower for FP32 (its update phase carries no FP64 work) and for the
-// batch kernel.  PREFETCH (split form only): phase D's stored values are
-// loaded into registers before phase C.
+// two threads per cell of a plane.  The plain FP64 kernel uses it.  The
+// FP32-bulk plain kernels keep the one-pass update phase instead, whose
+// threads without a cell start the next plane's flux phase early (kDyn):
+// that measured faster than the split for mixed and FP32.  PREFETCH (split
+// form only): phase D's stored values are loaded into registers before
+// phase C.
 template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false,
           bool SINGLE_BOX = false>
 struct StageKernel {
@@ -201,6 +203,8 @@ struct StageKernel {
   static constexpr int XO = T::XOFF;
   // TMA planes: plain kernels with 4-byte primitives
   static constexpr bool kTMA = tma_planes<PREC, MODE, SINGLE_BOX>();
+  static constexpr bool kDyn = !SPLIT && MODE == FM_PLAIN && !SLOPES;   // dynamic flux phase (see fluxes)
+  static constexpr int kLoadBarrier = 2, kPlaneBarrier = 3;            // named barriers of that form
   static_assert(!kTMA || ((8 * T::nR * sizeof(R)) % 128 == 0 && (T::oBN * sizeof(R)) % 128 == 0 &&
                           (T::nBslot * sizeof(R)) % 128 == 0 && (T::W * sizeof(R)) % 16 == 0),
                 "TMA ring slots must start on 128-byte boundaries and rows span whole 16-byte units");
@@ -337,12 +341,40 @@ struct StageKernel {
   // one reconstruction + Riemann + store path: only the stencil gather
   // depends on the face's axis, so a warp whose items straddle two axes
   // still solves once.
-  static __device__ __forceinline__ void fluxes(const Geo& g, R* sm, int k, int q, bool with_z) {
+  // kDyn: the one-pass update phase leaves the threads from nC on without a
+  // cell, and no barrier of the whole CTA separates the update phase of
+  // plane k from the flux phase of plane k + 1 (the update phase reads none
+  // of the arrays the flux phase writes).  Those threads start the next flux
+  // phase while the others finish their cells, once its plane is in: a TMA
+  // plane by its mbarrier, a gathered plane (which they load themselves) by a
+  // named barrier among them; the cell threads wait for the gathered plane on
+  // a second named barrier.  The flux items go to warps 32 at a time from a
+  // shared ticket counter.
+  static __device__ __forceinline__ void fluxes(const Geo& g, R* sm, int k, int q, bool with_z, int* ticket) {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
     const R gam = gpar<R>(g.gamma, g.fgamma);
     const R ig = R(1) / (gam - R(1));
-    for (int w = threadIdx.x; w < nitems; w += blockDim.x) {
+    if constexpr (kDyn) {
+      const int first = (int)blockDim.x > T::nC ? T::nC : 0;   // threads without a cell first
+      if ((int)threadIdx.x >= first) cell_emf(sm, q, (int)threadIdx.x - first, (int)blockDim.x - first);
+      const int lane = threadIdx.x & 31;
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(ticket, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= nitems) break;
+        if (base + lane < nitems) flux_item(g, sm, k, q, nZ, base + lane, gam, ig);
+      }
+    } else {
+      for (int w = threadIdx.x; w < nitems; w += blockDim.x) flux_item(g, sm, k, q, nZ, w, gam, ig);
+      cell_emf(sm, q, threadIdx.x, blockDim.x);
+    }
+  }
+
+  // one flux item of phase B: reconstruction, Riemann flux, store
+  static __device__ __forceinline__ void flux_item(const Geo& g, R* sm, int k, int q, int nZ, int w, R gam, R ig) {
+    {
       R c[4][7], wl[7], wr[7], f[7], bn, cm;
       int o;
       if (CHAR) {
@@ -352,7 +384,7 @@ struct StageKernel {
         if (g.riemann == 1) hll_flux_g(wl, wr, bn, gam, ig, f, &cm);
         else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
         store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
-        continue;
+        return;
       }
       const int D = item_stencil(sm, k, q, nZ, w, c, bn, o);
       plm_face(c[0], c[1], c[2], c[3], wl, wr, gpar<R>(g.rho_floor, g.frho_floor), gpar<R>(g.p_floor, g.fp_floor));
@@ -360,7 +392,6 @@ struct StageKernel {
       else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
     }
-    cell_emf(sm, q);
   }
 
   // ------------------------------------------------------------- phase B0
@@ -467,14 +498,15 @@ struct StageKernel {
       else hlld_flux_g(wl, wr, bn, gam, ig, f, &cm);
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
     }
-    cell_emf(sm, q);
+    cell_emf(sm, q, threadIdx.x, blockDim.x);
   }
 
   // cell-centred E_c = -v x B_c of plane q
-  static __device__ __forceinline__ void cell_emf(R* sm, int q) {
+  // (items w0, w0 + step, ...)
+  static __device__ __forceinline__ void cell_emf(R* sm, int q, int w0, int step) {
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
     R* EC = sm + T::oEC + (q & 1) * 3 * T::nZ;
-    for (int w = threadIdx.x; w < T::nZ; w += blockDim.x) {
+    for (int w = w0; w < T::nZ; w += step) {
       const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
       const int r = (i + XO) + W * (j + 2);
       const R vx = Pq[1 * T::nR + r], vy = Pq[2 * T::nR + r], vz = Pq[3 * T::nR + r];
@@ -649,7 +681,7 @@ struct StageKernel {
       }
       store_any(D, g, sm, q, o, f, cm, wl[0], wr[0]);
     }
-    cell_emf(sm, q);
+    cell_emf(sm, q, threadIdx.x, blockDim.x);
   }
 
   // ---------------------------------------------------------------- phase C
@@ -1119,6 +1151,8 @@ struct StageKernel {
       else rowc[t - T::W] = wrapc(gj0 - 2 + (t - T::W), g.n[1], g.bc[1]);
     }
     if (LEARN && threadIdx.x < 4) qcnt[threadIdx.x] = 0;
+    int* ticket = qcnt + 6;   // flux tickets of the dynamic flux phase, by plane parity
+    if (kDyn && threadIdx.x < 2) ticket[threadIdx.x] = 0;
     // the stage's dt: explicit, or cfl / (CFL max of the step's start), one
     // FP64 division per CTA
     int* dtw = qcnt + 4;
@@ -1154,7 +1188,7 @@ struct StageKernel {
       } else if constexpr (LEARN) {
         fluxes_learned(g, a, sm, queue, qcnt, 0, 1, true, gi0, gj0, kb, ke, nh, nd);
       } else {
-        fluxes(g, sm, 0, 1, true);
+        fluxes(g, sm, 0, 1, true, ticket);
       }
       __syncthreads();
       edges_2d(g, sm);
@@ -1197,7 +1231,7 @@ struct StageKernel {
     } else if constexpr (LEARN) {
       fluxes_learned(g, a, sm, queue, qcnt, kb - 2, kb - 1, false, gi0, gj0, kb, ke, nh, nd);
     } else {
-      fluxes(g, sm, kb - 2, kb - 1, false);
+      fluxes(g, sm, kb - 2, kb - 1, false, ticket + (kb & 1));
     }
     __syncthreads();
     // a TMA plane is issued as soon as the flux phase has freed its slot:
@@ -1211,8 +1245,19 @@ struct StageKernel {
       // the threads without a cell in the update phase load the next plane
       // while the others finish that phase (unless it comes by TMA)
       const bool tma_next = plane_tma(k + 2);
-      if (!tma_next) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true, T::nC < (int)blockDim.x ? T::nC : 0);
-      __syncthreads();
+      const int nl = (int)blockDim.x - T::nC;   // threads without a cell in the update phase
+      if (kDyn && !tma_next && nl >= 32 && nl % 32 == 0) {
+        if ((int)threadIdx.x >= T::nC) {
+          load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true, T::nC);
+          asm volatile("bar.sync %0, %1;" ::"r"(kLoadBarrier), "r"(nl) : "memory");
+          asm volatile("bar.arrive %0, %1;" ::"r"(kPlaneBarrier), "r"((int)blockDim.x) : "memory");
+        } else {
+          asm volatile("bar.sync %0, %1;" ::"r"(kPlaneBarrier), "r"((int)blockDim.x) : "memory");
+        }
+      } else {
+        if (!tma_next) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, k + 2, true, T::nC < (int)blockDim.x ? T::nC : 0);
+        if (!(kDyn && tma_next)) __syncthreads();
+      }
       if (tma_next) tma_wait(a, mbar, (k + 2) & 3, phases);
       if constexpr (SLOPES) {
         slopes(g, sm, sl, k + 1, false);
@@ -1221,9 +1266,12 @@ struct StageKernel {
       } else if constexpr (LEARN) {
         fluxes_learned(g, a, sm, queue, qcnt, k, k + 1, true, gi0, gj0, kb, ke, nh, nd);
       } else {
-        fluxes(g, sm, k, k + 1, true);
+        fluxes(g, sm, k, k + 1, true, ticket + (k & 1));
       }
       __syncthreads();
+      // the next flux phase's tickets: last drawn by the flux phase of plane
+      // k - 1, first drawn after the barrier that follows phase C
+      if (kDyn && threadIdx.x == 0) ticket[(k + 1) & 1] = 0;
       if (k + 3 <= ke + 1 && plane_tma(k + 3) && threadIdx.x == 0) {
         tma_issue(*tm, sm, mbar, k + 3, wrapc(k + 3, g.n[2], g.bc[2]), gi0, gj0, true, g, a.status);
         ++ntma;
@@ -1268,7 +1316,7 @@ __host__ __device__ constexpr int stage_min_blocks() {
 
 template <int PREC, int TX, int TY>
 __host__ __device__ constexpr bool stage_split() {
-  return PREC != P_FP32 && (TX * TY) % 32 == 0 && 2 * TX * TY <= stage_threads<PREC, TX, TY>();
+  return PREC == P_FP64 && (TX * TY) % 32 == 0 && 2 * TX * TY <= stage_threads<PREC, TX, TY>();
 }
 
 template <int PREC, int STAGE, int TX, int TY>

@@ -105,3 +105,30 @@ def perturbed(cell, face, rel=6e-8, seed=0):
     c = np.asarray(cell, np.float64) * (1.0 + rel * rng.choice([-1.0, 1.0], size=np.shape(cell)))
     f = [np.asarray(x, np.float64) * (1.0 + rel * rng.choice([-1.0, 1.0], size=np.shape(x))) for x in face]
     return np.ascontiguousarray(c), [np.ascontiguousarray(x) for x in f]
+
+
+# Relative input noise of a form's rounding (4 ulp in FP64; half an FP32 ulp
+# for the FP32-bulk forms) and the relative error with which a form computes
+# the quantities its branch thresholds decide on (the mass flux against the
+# upwind deadband: ~1e-7 of rho c against 1e-6 in the FP32-bulk forms).
+NOISE = {"fp64": 4 * 2.0 ** -53, "mixed": 6e-8, "fp32": 6e-8}
+THRESH_SPREAD = {"fp64": 1e-5, "mixed": 0.1, "fp32": 0.1}
+
+
+def control(cfg, cell, face, dts, rc, rf, precision):
+    """How far the oracle's own result (rc, rf after the steps dts) moves
+    under the rounding of the form's precision: input noise (two seeds) and
+    branch thresholds scaled by 1 -/+ the decided quantities' relative error.
+    Returns the per-variable relative L1 and the per-element figure, each the
+    largest over the four runs."""
+    runs = [(perturbed(cell, face, rel=NOISE[precision], seed=seed), 1.0) for seed in (1, 2)]
+    runs += [((cell, face), 1.0 + s * THRESH_SPREAD[precision]) for s in (-1.0, 1.0)]
+    move, elem = {}, 0.0
+    for (c0, f0), scale in runs:
+        cfg.thresh_scale = scale
+        pc, pf = O.step_dts(cfg, c0, f0, dts)
+        e = state_errors(pc, pf, rc, rf)
+        move = {k: max(move.get(k, 0.0), v) for k, v in e.items()}
+        elem = max(elem, max_elementwise_rel(pc, pf, rc, rf)[0])
+    cfg.thresh_scale = 1.0
+    return move, elem

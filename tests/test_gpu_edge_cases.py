@@ -28,33 +28,13 @@ import pytest
 
 import oracle as O
 from edge_cases import CASES
-from helpers import max_elementwise_rel, ocfg, perturbed, state_errors
+from helpers import control, max_elementwise_rel, ocfg, state_errors
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-5}
 ELEM_TOL_FP64 = 1e-10
 NSTEPS = 3
-NOISE = {"fp64": 4 * 2.0 ** -53, "mixed": 6e-8}
-THRESH_SPREAD = {"fp64": 1e-5, "mixed": 0.1}
-
-
-def control(cfg, box, dts, rc, rf, precision):
-    """How far the oracle's own result moves under the rounding of the
-    form's precision: input noise (two seeds) and branch thresholds scaled
-    by 1 -/+ the decided quantities' relative error.  Returns the per-variable
-    relative L1 and the per-element figure, each the largest over the runs."""
-    runs = [(perturbed(box.cell, box.face, rel=NOISE[precision], seed=seed), 1.0) for seed in (1, 2)]
-    runs += [((box.cell, box.face), 1.0 + s * THRESH_SPREAD[precision]) for s in (-1.0, 1.0)]
-    move, elem = {}, 0.0
-    for (c0, f0), scale in runs:
-        cfg.thresh_scale = scale
-        pc, pf = O.step_dts(cfg, c0, f0, dts)
-        e = state_errors(pc, pf, rc, rf)
-        move = {k: max(move.get(k, 0.0), v) for k, v in e.items()}
-        elem = max(elem, max_elementwise_rel(pc, pf, rc, rf)[0])
-    cfg.thresh_scale = 1.0
-    return move, elem
 
 
 def _run(box, precision, dts):
@@ -80,7 +60,7 @@ def test_edge_case_parity(case, precision):
     assert st["status"] == 0, st
     errs = state_errors(c, f, rc, rf)
     worst = max_elementwise_rel(c, f, rc, rf)
-    move, move_elem = control(cfg, box, dts, rc, rf, precision)
+    move, move_elem = control(cfg, box.cell, box.face, dts, rc, rf, precision)
     tol = {k: max(TOL[precision], 3.0 * move[k]) for k in errs}
     print(f"{case} {precision}: max L1 {max(errs.values()):.2e} (oracle movement {max(move.values()):.2e}), "
           f"max per element {worst[0]:.2e} ({worst[1]}; oracle movement {move_elem:.2e})")
