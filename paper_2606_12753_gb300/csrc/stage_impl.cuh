@@ -183,12 +183,12 @@ __host__ __device__ constexpr int ring_xo() {
 
 // SPLIT: the update phase splits each cell between two threads (face group
 // and conserved group, named-barrier hand-over); the CTA then needs at least
-// two threads per cell of a plane.  The plain FP64 kernel uses it.  The
-// FP32-bulk plain kernels keep the one-pass update phase instead, whose
-// threads without a cell start the next plane's flux phase early (kDyn):
-// that measured faster than the split for mixed and FP32.  PREFETCH (split
-// form only): phase D's stored values are loaded into registers before
-// phase C.
+// two threads per cell of a plane.  The learned-switch and characteristic
+// kernels of the mixed and FP64 forms use it.  The plain kernels keep the
+// one-pass update phase instead, whose threads without a cell start the next
+// plane's flux (or slope) phase early (kDyn): that measured faster than the
+// split in every form.  PREFETCH (split form only): phase D's stored values
+// are loaded into registers before phase C.
 template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false,
           bool SINGLE_BOX = false>
 struct StageKernel {
@@ -203,7 +203,7 @@ struct StageKernel {
   static constexpr int XO = T::XOFF;
   // TMA planes: plain kernels with 4-byte primitives
   static constexpr bool kTMA = tma_planes<PREC, MODE, SINGLE_BOX>();
-  static constexpr bool kDyn = !SPLIT && MODE == FM_PLAIN && !SLOPES;   // dynamic flux phase (see fluxes)
+  static constexpr bool kDyn = !SPLIT && MODE == FM_PLAIN;   // dynamic flux or slope phase (see fluxes)
   static constexpr int kLoadBarrier = 2, kPlaneBarrier = 3;            // named barriers of that form
   static_assert(!kTMA || ((8 * T::nR * sizeof(R)) % 128 == 0 && (T::oBN * sizeof(R)) % 128 == 0 &&
                           (T::nBslot * sizeof(R)) % 128 == 0 && (T::W * sizeof(R)) % 16 == 0),
@@ -398,12 +398,30 @@ struct StageKernel {
   // Half slopes of plane q's cells over the (TX+2) x (TY+2) grid the faces touch:
   // x and y (for the x-, y-faces of plane q) and z (for the z-faces on both
   // sides of plane q; kept by parity).  zonly: only the z slopes.
-  static __device__ __forceinline__ void slopes(const Geo& g, R* sm, R* sl, int q, bool zonly) {
+  // ticket: draw the items 32 at a time per warp (kDyn), or null (static).
+  static __device__ __forceinline__ void slopes(const Geo& g, R* sm, R* sl, int q, bool zonly, int* ticket) {
+    constexpr int n = T::nZ;
+    const int first = zonly ? 2 * n : 0;
+    if (kDyn && ticket) {
+      const int lane = threadIdx.x & 31;
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(ticket, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (first + base >= 3 * n) break;
+        if (first + base + lane < 3 * n) slope_item(g, sm, sl, q, first + base + lane);
+      }
+    } else {
+      for (int it = first + threadIdx.x; it < 3 * n; it += blockDim.x) slope_item(g, sm, sl, q, it);
+    }
+  }
+
+  // half slopes of one cell along one axis (item it = axis * nZ + cell)
+  static __device__ __forceinline__ void slope_item(const Geo& g, R* sm, R* sl, int q, int it) {
     const R* Pq = sm + T::oP + (q & 3) * 8 * T::nR;
     const R gam = gpar<R>(g.gamma, g.fgamma);
     constexpr int n = T::nZ;
-    const int first = zonly ? 2 * n : 0;
-    for (int it = first + threadIdx.x; it < 3 * n; it += blockDim.x) {
+    {
       const int D = it / n, cidx = it - D * n;
       const int i = cidx % (TX + 2) - 1, j = cidx / (TX + 2) - 1;
       const int r = MHD_SIDX(MHD_SIDX((i + XO) + W * (j + 2) - W - 1, T::nR - 2 * W - 2) + W + 1, T::nR);
@@ -1010,10 +1028,10 @@ struct StageKernel {
   // phase reads (face thread: its six faces, the lower z-face only when not
   // carried; conserved-value thread: its five values) are loaded into
   // registers before phase C, so that the loads are in flight while the
-  // edges are formed.  Chosen for kernels with registers to spare (plain
-  // FP64, characteristic reconstruction); in the kernels capped at 80 or 128
-  // registers (FP32-bulk, learned switch) the held values spill, and a
-  // cp.async copy into the idle ring slot measured slower there too.
+  // edges are formed.  Chosen for the characteristic kernels, which have
+  // registers to spare; in the kernels capped at 80 or 128 registers
+  // (FP32-bulk, learned switch) the held values spill, and a cp.async copy
+  // into the idle ring slot measured slower there too.
   static constexpr bool kPF = SPLIT && PREFETCH;
   struct Pre {
     Old o[6];
@@ -1181,8 +1199,8 @@ struct StageKernel {
       for (int m = -1; m <= 2; ++m) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, m, m == 0 || m == 1);
       __syncthreads();
       if constexpr (SLOPES) {
-        slopes(g, sm, sl, 0, true);
-        slopes(g, sm, sl, 1, false);
+        slopes(g, sm, sl, 0, true, nullptr);
+        slopes(g, sm, sl, 1, false, nullptr);
         __syncthreads();
         fluxes_sl(g, sm, sl, 0, 1, true);
       } else if constexpr (LEARN) {
@@ -1225,7 +1243,7 @@ struct StageKernel {
     for (int m = kb - 2; m <= kb; ++m)
       if (plane_tma(m)) tma_wait(a, mbar, m & 3, phases);
     if constexpr (SLOPES) {
-      slopes(g, sm, sl, kb - 1, false);
+      slopes(g, sm, sl, kb - 1, false, ticket + (kb & 1));
       __syncthreads();
       fluxes_sl(g, sm, sl, kb - 2, kb - 1, false);
     } else if constexpr (LEARN) {
@@ -1260,7 +1278,7 @@ struct StageKernel {
       }
       if (tma_next) tma_wait(a, mbar, (k + 2) & 3, phases);
       if constexpr (SLOPES) {
-        slopes(g, sm, sl, k + 1, false);
+        slopes(g, sm, sl, k + 1, false, ticket + (k & 1));
         __syncthreads();
         fluxes_sl(g, sm, sl, k, k + 1, true);
       } else if constexpr (LEARN) {
@@ -1314,16 +1332,11 @@ __host__ __device__ constexpr int stage_min_blocks() {
   return PREC == P_FP64 ? (TX * TY <= 64 ? 2 : 1) : 768 / stage_threads<PREC, TX, TY>();
 }
 
-template <int PREC, int TX, int TY>
-__host__ __device__ constexpr bool stage_split() {
-  return PREC == P_FP64 && (TX * TY) % 32 == 0 && 2 * TX * TY <= stage_threads<PREC, TX, TY>();
-}
-
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(stage_threads<PREC, TX, TY>(), stage_min_blocks<PREC, TX, TY>())
     stage_kernel(Geo g, StageArgs a, const __grid_constant__ TmaMaps tm) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, stage_split<PREC, TX, TY>(), PREC == P_FP64, true>::run_item(
+  StageKernel<PREC, STAGE, TX, TY, FM_PLAIN, false, false, true>::run_item(
       g, a, blockIdx.x, smem_raw, &tm);
 }
 
