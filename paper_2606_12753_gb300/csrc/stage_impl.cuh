@@ -183,12 +183,12 @@ __host__ __device__ constexpr int ring_xo() {
 
 // SPLIT: the update phase splits each cell between two threads (face group
 // and conserved group, named-barrier hand-over); the CTA then needs at least
-// two threads per cell of a plane.  The learned-switch and characteristic
-// kernels of the mixed and FP64 forms use it.  The plain kernels keep the
-// one-pass update phase instead, whose threads without a cell start the next
+// two threads per cell of a plane.  The learned-switch kernels of the mixed
+// and FP64 forms and the mixed characteristic kernel use it.  The others keep
+// the one-pass update phase, whose threads without a cell start the next
 // plane's flux (or slope) phase early (kDyn): that measured faster than the
-// split in every form.  PREFETCH (split form only): phase D's stored values
-// are loaded into registers before phase C.
+// split there.  PREFETCH (split form only): phase D's stored values are
+// loaded into registers before phase C.
 template <int PREC, int STAGE, int TX, int TY, int MODE = FM_PLAIN, bool SPLIT = false, bool PREFETCH = false,
           bool SINGLE_BOX = false>
 struct StageKernel {
@@ -203,7 +203,7 @@ struct StageKernel {
   static constexpr int XO = T::XOFF;
   // TMA planes: plain kernels with 4-byte primitives
   static constexpr bool kTMA = tma_planes<PREC, MODE, SINGLE_BOX>();
-  static constexpr bool kDyn = !SPLIT && MODE == FM_PLAIN;   // dynamic flux or slope phase (see fluxes)
+  static constexpr bool kDyn = !SPLIT && MODE != FM_LEARNED;   // dynamic flux or slope phase (see fluxes)
   static constexpr int kLoadBarrier = 2, kPlaneBarrier = 3;            // named barriers of that form
   static_assert(!kTMA || ((8 * T::nR * sizeof(R)) % 128 == 0 && (T::oBN * sizeof(R)) % 128 == 0 &&
                           (T::nBslot * sizeof(R)) % 128 == 0 && (T::W * sizeof(R)) % 16 == 0),
@@ -1028,7 +1028,7 @@ struct StageKernel {
   // phase reads (face thread: its six faces, the lower z-face only when not
   // carried; conserved-value thread: its five values) are loaded into
   // registers before phase C, so that the loads are in flight while the
-  // edges are formed.  Chosen for the characteristic kernels, which have
+  // edges are formed.  Chosen for the mixed characteristic kernel, which has
   // registers to spare; in the kernels capped at 80 or 128 registers
   // (FP32-bulk, learned switch) the held values spill, and a cp.async copy
   // into the idle ring slot measured slower there too.
@@ -1352,7 +1352,7 @@ __global__ void __launch_bounds__(256, PREC == P_FP64 ? 2 : 3) stage_kernel_lear
 template <int PREC, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(256, PREC == P_FP64 ? 1 : 2) stage_kernel_char(Geo g, StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  StageKernel<PREC, STAGE, TX, TY, FM_CHAR, PREC != P_FP32 && 2 * TX * TY <= 256, true>::run_item(g, a, blockIdx.x,
+  StageKernel<PREC, STAGE, TX, TY, FM_CHAR, PREC == P_MIXED && 2 * TX * TY <= 256, true>::run_item(g, a, blockIdx.x,
                                                                                                    smem_raw);
 }
 
