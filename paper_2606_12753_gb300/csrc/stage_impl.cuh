@@ -341,6 +341,7 @@ struct StageKernel {
   // one reconstruction + Riemann + store path: only the stencil gather
   // depends on the face's axis, so a warp whose items straddle two axes
   // still solves once.
+  // ticket null: the items by thread index (the single plane of a 2D box).
   // kDyn: the one-pass update phase leaves the threads from nC on without a
   // cell, and no barrier of the whole CTA separates the update phase of
   // plane k from the flux phase of plane k + 1 (the update phase reads none
@@ -355,7 +356,7 @@ struct StageKernel {
     const int nitems = nZ + T::nX + T::nY;
     const R gam = gpar<R>(g.gamma, g.fgamma);
     const R ig = R(1) / (gam - R(1));
-    if constexpr (kDyn) {
+    if (kDyn && ticket) {
       const int first = (int)blockDim.x > T::nC ? T::nC : 0;   // threads without a cell first
       if ((int)threadIdx.x >= first) cell_emf(sm, q, (int)threadIdx.x - first, (int)blockDim.x - first);
       const int lane = threadIdx.x & 31;
@@ -779,7 +780,12 @@ struct StageKernel {
     R* DU0 = sm + T::oDU;
     const R* HX = sm + T::oHX;
     const R* HY = sm + T::oHY;
-    for (int c = threadIdx.x; c < T::nC; c += blockDim.x) {
+    // edge slots on whole warps from warp 0, cells on the warps after them (as in phase C)
+    constexpr int kEdgeThreads = (T::nE + 31) / 32 * 32;
+    const bool apart = (int)blockDim.x >= kEdgeThreads + 64;
+    const int c0 = apart ? (int)threadIdx.x - kEdgeThreads : (int)threadIdx.x;
+    const int cstep = apart ? (int)blockDim.x - kEdgeThreads : (int)blockDim.x;
+    for (int c = c0 < 0 ? T::nC : c0; c < T::nC; c += cstep) {
       const int i = c % TX, j = c / TX;
       const int ixm = i + (TX + 1) * (j + 1), ixp = ixm + 1;
       const int iym = (i + 1) + (TX + 2) * j, iyp = iym + (TX + 2);
@@ -799,7 +805,7 @@ struct StageKernel {
     R* EX1 = sm + T::oEXY + 2 * T::nE;
     R* EY1 = EX1 + T::nE;
     constexpr int nX = T::nX, nY = T::nY, nZ = T::nZ;
-    for (int e = threadIdx.x; e < T::nE; e += blockDim.x) {
+    for (int e = threadIdx.x; e < T::nE; e += apart ? kEdgeThreads : (int)blockDim.x) {
       const int i = e % (TX + 1), j = e / (TX + 1);
       {
         const int xa = i + (TX + 1) * j, xb = xa + (TX + 1);
@@ -1056,14 +1062,22 @@ struct StageKernel {
 
   // zc: the face group's z-face carry (split form; reset at a chunk's
   // first plane); pre: the values prefetch() fetched for this plane (nullptr:
-  // none were)
+  // none were).  single_plane: the item's only plane (a two-dimensional box),
+  // which no flux phase follows: the single-box mixed and FP64 kernels split
+  // its cells between two threads even in the one-pass form, whose other
+  // threads would otherwise idle there.
+  static constexpr bool kCanSplit =
+      SPLIT || (SINGLE_BOX && PREC != P_FP32 && T::nC % 32 == 0 &&
+                (size_t)5 * T::nC * sizeof(double) <= (size_t)5 * (T::nX + T::nY + T::nZ) * sizeof(R));
   static __device__ __forceinline__ void update_plane(const Geo& g, const StageArgs& a, R* sm, const StepDt& dt,
                                                       int gi0, int gj0, int k, unsigned& nrho, unsigned& np,
-                                                      bool& bad, R& smax, ZCarry& zc, const Pre* pre = nullptr) {
+                                                      bool& bad, R& smax, ZCarry& zc, const Pre* pre = nullptr,
+                                                      bool single_plane = false) {
     const R* DU = sm + T::oDU + (k & 1) * 5 * T::nC;
     const int nx = g.n[0], ny = g.n[1];
     const int t = threadIdx.x;
-    if constexpr (SPLIT) {
+    if constexpr (kCanSplit) {
+      if (SPLIT || (single_plane && 2 * T::nC <= (int)blockDim.x)) {
       static_assert(T::nC % 32 == 0, "the split update phase needs whole warps per group");
       double* U5 = reinterpret_cast<double*>(sm + T::oHX);   // [5][nC], in the idle flux arrays
       static_assert((size_t)5 * T::nC * sizeof(double) <= (size_t)5 * (T::nX + T::nY + T::nZ) * sizeof(R),
@@ -1093,7 +1107,8 @@ struct StageKernel {
       for (int v = 0; v < 5; ++v) u[v] = U5[v * T::nC + c];
       recover_cell(g, a, s, u, b, nrho, np, bad, smax);
       return;
-    } else {
+      }
+    }
     for (int c = t; c < T::nC; c += blockDim.x) {
       const int i = c % TX, j = c / TX;
       const int gi = gi0 + i, gj = gj0 + j;
@@ -1104,7 +1119,6 @@ struct StageKernel {
       advance_cell(g, a, DU, dt, c, s, u);
       if (!a.Wout) continue;   // operator evaluation only (mhd_rhs)
       recover_cell(g, a, s, u, b, nrho, np, bad, smax);
-    }
     }
   }
 
@@ -1196,7 +1210,19 @@ struct StageKernel {
       // plane 0, so one flux pass (the z-faces, which feed E_x and E_y, and
       // the x/y faces of the plane) replaces the chunk prologue and the
       // first plane of the 3D march.
-      for (int m = -1; m <= 2; ++m) load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, m, m == 0 || m == 1);
+      // the plane is gathered once; the other ring slots (planes -1, 1, 2) and
+      // the second lower-face slot are shared-memory copies of it
+      load_plane(g, a, sm, colc, rowc, dt, gi0, gj0, 0, true);
+      __syncthreads();
+      {
+        const R* P0 = sm + T::oP;
+        for (int e = threadIdx.x; e < 8 * T::nR; e += blockDim.x) {
+          const R v = P0[e];
+#pragma unroll
+          for (int m = 1; m < 4; ++m) sm[T::oP + m * 8 * T::nR + e] = v;
+        }
+        for (int e = threadIdx.x; e < T::nBslot; e += blockDim.x) sm[T::oBN + T::nBslot + e] = sm[T::oBN + e];
+      }
       __syncthreads();
       if constexpr (SLOPES) {
         slopes(g, sm, sl, 0, true, nullptr);
@@ -1206,13 +1232,13 @@ struct StageKernel {
       } else if constexpr (LEARN) {
         fluxes_learned(g, a, sm, queue, qcnt, 0, 1, true, gi0, gj0, kb, ke, nh, nd);
       } else {
-        fluxes(g, sm, 0, 1, true, ticket);
+        fluxes(g, sm, 0, 1, true, nullptr);   // all threads start together: static items
       }
       __syncthreads();
       edges_2d(g, sm);
       __syncthreads();
       ZCarry zc{S(0), R(0), false};
-      update_plane(g, a, sm, sdt, gi0, gj0, 0, nrho, np, bad, smax, zc);
+      update_plane(g, a, sm, sdt, gi0, gj0, 0, nrho, np, bad, smax, zc, nullptr, true);
       finish(a, nrho, np, nh, nd, bad, smax);
       fold_bounds_flag(a);
       return;
