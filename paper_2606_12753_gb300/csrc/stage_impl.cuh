@@ -225,8 +225,12 @@ struct StageKernel {
     const R* Win = (const R*)a.Win;
     const int t = (int)threadIdx.x - t0;
     if (t < 0) return;
-    for (int r = t; r < T::nR; r += (int)blockDim.x - t0) {
-      const int x = r % W, y = r / W;
+    // the ring columns the stencil reads: XO - 2 .. XO + TX + 1 (a padded
+    // ring's outer columns are for the 16-byte rule of TMA boxes only)
+    constexpr int WR = TX + 4;
+    for (int rr = t; rr < WR * T::H; rr += (int)blockDim.x - t0) {
+      const int x = XO - 2 + rr % WR, y = rr / WR;
+      const int r = x + W * y;
       const int gi = gi0 - XO + x, gj = gj0 - 2 + y;
       const bool inside = zin && (g.bc[0] == 0 || (gi >= 0 && gi < g.n[0])) &&
                           (g.bc[1] == 0 || (gj >= 0 && gj < g.n[1]));
