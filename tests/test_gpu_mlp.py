@@ -190,3 +190,31 @@ def test_training_lowers_the_loss():
         mhd.mlp_adam(blk.data_ptr(), m.data_ptr(), v.data_ptr(), g.data_ptr(), step, lr=3e-3)
     l1 = loss()
     assert np.isfinite(l1) and l1 < 0.7 * l0, (l0, l1)
+
+
+@pytest.mark.parametrize("n", [1, 5, 127, 128, 129, 300])
+def test_forward_and_backward_on_partial_tiles(n):
+    """The tensor-core kernels take 128 rows per tile; row counts below,
+    at and just past a tile (rows past n are zero in the products and add
+    nothing to the gradient) match the reference."""
+    import torch
+    from paper_2606_12753_gb300 import mhd
+    params = _params(11)
+    X = _x(n, 12)
+    rng = np.random.default_rng(13)
+    y = (rng.uniform(size=n) < 0.4).astype(np.float32)
+    blk = _block(torch, params)
+    xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    zd = torch.empty(n, dtype=torch.float32, device="cuda")
+    gd = torch.zeros(M.NPARAM, dtype=torch.float32, device="cuda")
+    mhd.mlp_forward(blk.data_ptr(), xd.data_ptr(), n, zd.data_ptr())
+    mhd.mlp_backward(blk.data_ptr(), xd.data_ptr(), yd.data_ptr(), n, gd.data_ptr())
+    torch.cuda.synchronize()
+    params32 = M.unflatten(M.flatten(params).astype(np.float32).astype(np.float64))
+    zr, cache = M.forward(params32, X.astype(np.float64), bf16_inputs=True)
+    z = zd.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(z))
+    assert np.abs(z - zr).max() <= 2e-2 * (1 + np.abs(zr).max())
+    gr = M.flatten(M.backward(cache, zr, y.astype(np.float64), bf16_deltas=True))
+    g = gd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - gr) <= 5e-3 * np.linalg.norm(gr), np.linalg.norm(g - gr) / np.linalg.norm(gr)
