@@ -167,8 +167,10 @@ constexpr bool slopes_in_smem() {
 }
 
 // Whether a kernel takes interior planes by TMA: the plain single-box stage
-// kernels with 4-byte primitives (mixed, FP32).  The batch kernel, whose
-// small outflow boxes have few interior tiles, gathers every plane.
+// kernels with 4-byte primitives (mixed, FP32).  The batch kernel gathers
+// every plane: its small outflow boxes have few interior tiles, and a tensor
+// map needs rows that are a multiple of 16 bytes, which few of its boxes of
+// arbitrary width have.
 template <int PREC, int MODE, bool SINGLE_BOX>
 __host__ __device__ constexpr bool tma_planes() {
   return SINGLE_BOX && PREC != P_FP64 && MODE == FM_PLAIN;
