@@ -39,14 +39,16 @@ cudaError_t MHD_UNIT_FN(batch_set_smem)(int tx, int ty, size_t bytes) {
 }
 
 // dynamic shared memory of the batch kernel of a tile (the plain stage layout
-// with the unpadded ring; 0: not instantiated)
+// with the unpadded ring and, without a slope phase, the tile's item list;
+// 0: not instantiated)
 size_t MHD_UNIT_FN(batch_smem_bytes)(int tx, int ty) {
   using R = Prec<MHD_UNIT_PREC>::R;
   using S = Prec<MHD_UNIT_PREC>::S;
 #define X(TXv, TYv)                                                                                      \
   if (tx == TXv && ty == TYv)                                                                            \
     return Tile<TXv, TYv, ring_xo<MHD_UNIT_PREC, FM_PLAIN, false>()>::bytes<                             \
-        R, S, slopes_in_smem<MHD_UNIT_PREC, FM_PLAIN, TXv, TYv>()>();
+        R, S, slopes_in_smem<MHD_UNIT_PREC, FM_PLAIN, TXv, TYv>(),                                       \
+        compact_items<MHD_UNIT_PREC, FM_PLAIN, false, TXv, TYv>()>();
   MHD_BATCH_TILES(X)
 #undef X
   return 0;

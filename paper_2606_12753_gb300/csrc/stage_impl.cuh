@@ -66,7 +66,7 @@ struct Tile {
   static constexpr int nItems = nZ + nX + nY;
   // index tables (int): colc[W], rowc[H], then the queue counters of the
   // learned switch (HLL and HLLD items, one pair per plane parity)
-  static constexpr int nI = W + H + 8;   // column/row maps, switch counters, the stage's dt, flux tickets
+  static constexpr int nI = W + H + 9;   // column/row maps, switch counters, the stage's dt, flux tickets, item count
   // then four mbarriers (8 bytes each), one per ring slot, for TMA planes
   // per-cell half slopes (type R) over the (TX+2) x (TY+2) cells the faces touch:
   // x and y slopes of the current plane, z slopes of two planes (by parity)
@@ -176,6 +176,15 @@ __host__ __device__ constexpr bool tma_planes() {
   return SINGLE_BOX && PREC != P_FP64 && MODE == FM_PLAIN;
 }
 
+// Whether a kernel solves, on a tile that the box edge cuts, only the flux
+// items its valid cells need (a per-tile list in shared memory, in the
+// learned switch's queue region): the batch kernel's plain forms without a
+// slope phase, whose boxes of arbitrary size leave many ragged tiles.
+template <int PREC, int MODE, bool SINGLE_BOX, int TX, int TY>
+__host__ __device__ constexpr bool compact_items() {
+  return !SINGLE_BOX && MODE == FM_PLAIN && !slopes_in_smem<PREC, MODE, TX, TY>();
+}
+
 // Ring x-offset of a kernel: kernels with TMA planes pad the ring rows (see
 // Tile); all others keep the 2-cell halo.
 template <int PREC, int MODE, bool SINGLE_BOX>
@@ -206,6 +215,8 @@ struct StageKernel {
   // TMA planes: plain kernels with 4-byte primitives
   static constexpr bool kTMA = tma_planes<PREC, MODE, SINGLE_BOX>();
   static constexpr bool kDyn = !SPLIT && MODE != FM_LEARNED;   // dynamic flux or slope phase (see fluxes)
+  static constexpr bool kCompact = kDyn && compact_items<PREC, MODE, SINGLE_BOX, TX, TY>();   // see build_items
+  static constexpr bool kQueue = LEARN || kCompact;   // the layout's queue region is in use
   static constexpr int kLoadBarrier = 2, kPlaneBarrier = 3;            // named barriers of that form
   static_assert(!kTMA || ((8 * T::nR * sizeof(R)) % 128 == 0 && (T::oBN * sizeof(R)) % 128 == 0 &&
                           (T::nBslot * sizeof(R)) % 128 == 0 && (T::W * sizeof(R)) % 16 == 0),
@@ -357,6 +368,8 @@ struct StageKernel {
   // named barrier among them; the cell threads wait for the gathered plane on
   // a second named barrier.  The flux items go to warps 32 at a time from a
   // shared ticket counter.
+  // kCompact: the items of the tile's list (build_items), which sits at fixed
+  // offsets from the shared-memory base.
   static __device__ __forceinline__ void fluxes(const Geo& g, R* sm, int k, int q, bool with_z, int* ticket) {
     const int nZ = with_z ? T::nZ : 0;
     const int nitems = nZ + T::nX + T::nY;
@@ -366,12 +379,27 @@ struct StageKernel {
       const int first = (int)blockDim.x > T::nC ? T::nC : 0;   // threads without a cell first
       if ((int)threadIdx.x >= first) cell_emf(sm, q, (int)threadIdx.x - first, (int)blockDim.x - first);
       const int lane = threadIdx.x & 31;
-      for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(ticket, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= nitems) break;
-        if (base + lane < nitems) flux_item(g, sm, k, q, nZ, base + lane, gam, ig);
+      if (kCompact && with_z) {
+        // the tile's list (a chunk's first pass, without z-faces, takes every item)
+        const unsigned char* base0 = reinterpret_cast<const unsigned char*>(sm);
+        const unsigned short* list =
+            reinterpret_cast<const unsigned short*>(base0 + T::template queue_off<R, kQueue>());
+        const int nl = reinterpret_cast<const int*>(base0 + T::template int_off<R, kQueue>())[T::W + T::H + 8];
+        for (;;) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(ticket, 32);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (base >= nl) break;
+          if (base + lane < nl) flux_item(g, sm, k, q, T::nZ, list[MHD_SIDX(base + lane, T::nItems)], gam, ig);
+        }
+      } else {
+        for (;;) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(ticket, 32);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (base >= nitems) break;
+          if (base + lane < nitems) flux_item(g, sm, k, q, nZ, base + lane, gam, ig);
+        }
       }
     } else {
       for (int w = threadIdx.x; w < nitems; w += blockDim.x) flux_item(g, sm, k, q, nZ, w, gam, ig);
@@ -1175,6 +1203,41 @@ struct StageKernel {
     }
   }
 
+  // The flux items a tile whose valid cells are the first vx x vy needs, in
+  // the order z-, x-, y-faces (full-tile numbering), by warp 0: z-faces at
+  // i in [-1, vx], j in [-1, vy]; x-faces at i in [0, vx], j in [-1, vy];
+  // y-faces at i in [-1, vx], j in [0, vy].  They are all that the divergence
+  // and the edge EMFs of the valid cells read; the other slots keep stale
+  // values that only cells outside the box would use.
+  static __device__ __forceinline__ void build_items(const Geo& g, unsigned short* list, int* lcnt, int gi0, int gj0) {
+    // (lcnt: the item count)
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int vx = min(TX, g.n[0] - gi0), vy = min(TY, g.n[1] - gj0);
+    int cnt = 0;
+#pragma unroll 1
+    for (int base = 0; base < T::nItems; base += 32) {
+      const int w = base + lane;
+      bool need = false;
+      if (w < T::nZ) {
+        const int i = w % (TX + 2) - 1, j = w / (TX + 2) - 1;
+        need = i <= vx && j <= vy;
+      } else if (w < T::nZ + T::nX) {
+        const int o = w - T::nZ;
+        const int i = o % (TX + 1), j = o / (TX + 1) - 1;
+        need = i <= vx && j <= vy;
+      } else if (w < T::nItems) {
+        const int o = w - T::nZ - T::nX;
+        const int i = o % (TX + 2) - 1, j = o / (TX + 2);
+        need = i <= vx && j <= vy;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, need);
+      if (need) list[MHD_SIDX(cnt + __popc(m & ((1u << lane) - 1u)), T::nItems)] = (unsigned short)w;
+      cnt += __popc(m);
+    }
+    if (lane == 0) *lcnt = cnt;
+  }
+
   // One work item: tile `item` (x fastest, then y, then z chunk) of one box.
   // Shared memory is the caller's dynamic allocation; every thread of the
   // CTA calls this with the same arguments.  tm: tensor maps of the stage's
@@ -1183,12 +1246,12 @@ struct StageKernel {
                                   const TmaMaps* tm = nullptr) {
     R* sm = reinterpret_cast<R*>(smem_raw);
     unsigned short* queue =
-        reinterpret_cast<unsigned short*>(smem_raw + T::template queue_off<R, LEARN>());   // learned switch only
-    int* colc = reinterpret_cast<int*>(smem_raw + T::template int_off<R, LEARN>());
+        reinterpret_cast<unsigned short*>(smem_raw + T::template queue_off<R, kQueue>());   // learned switch, item list
+    int* colc = reinterpret_cast<int*>(smem_raw + T::template int_off<R, kQueue>());
     int* rowc = colc + W;
     int* qcnt = rowc + T::H;
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw + T::template mbar_off<R, LEARN>());
-    constexpr size_t sl_off = T::template core_bytes<R, S, LEARN>();
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw + T::template mbar_off<R, kQueue>());
+    constexpr size_t sl_off = T::template core_bytes<R, S, kQueue>();
     R* sl = reinterpret_cast<R*>(smem_raw + sl_off);   // used when SLOPES
 
     int b = item;
@@ -1212,6 +1275,7 @@ struct StageKernel {
     if (LEARN && threadIdx.x < 4) qcnt[threadIdx.x] = 0;
     int* ticket = qcnt + 6;   // flux tickets of the dynamic flux phase, by plane parity
     if (kDyn && threadIdx.x < 2) ticket[threadIdx.x] = 0;
+    if constexpr (kCompact) build_items(g, queue, qcnt + 8, gi0, gj0);
     // the stage's dt: explicit, or cfl / (CFL max of the step's start), one
     // FP64 division per CTA
     int* dtw = qcnt + 4;
